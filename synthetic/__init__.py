@@ -1,0 +1,112 @@
+"""Seeded synthetic inputs shared by the oracle-side tests and the CUDA-side callers.
+
+This module only draws random numbers and lays out the silicon-like test cells.
+It holds none of the method's arithmetic (no Hamiltonian, no FFT, no exchange,
+no propagation): every quantity the method computes is computed separately by
+``oracle/`` and by the CUDA library.
+
+Workload recipe (the paper's test system, Sec. 4, is a silicon supercell built
+from simple-cubic 8-atom diamond cells with lattice constant 5.43 Angstrom,
+10 Ha planewave cutoff and a 50 as time step; the pseudopotential and the laser
+of the paper are replaced by Gaussian wells and a velocity-gauge kick):
+
+* cell: ``reps`` x ``reps`` x ``reps`` cubic diamond cells of edge 10.26 bohr;
+* atoms: the 8 diamond sites of each cell (fractional positions below);
+* orbitals: two electrons per atom, so ``n_orb = 4 * n_atoms / 2 = 16 reps**3``
+  doubly occupied orbitals (Si has 4 valence electrons);
+* initial coefficients: ``c_b(G) = (g1 + i g2) exp(-|G|^2 / 4)`` with ``g1, g2``
+  standard normal from ``numpy.random.Generator(PCG64(seed))``, drawn band by
+  band over the basis vectors in the order given by the caller (the basis is
+  the set of grid frequencies with |G|^2/2 <= ecut, listed by increasing
+  row-major flat grid index); these are NOT orthonormal, each side
+  orthonormalises them itself.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BOHR_PER_ANGSTROM = 1.8897261254578281
+# Simple-cubic diamond cell of the paper's test system (Sec. 4): 5.43 Angstrom.
+SI_CUBIC_CELL_BOHR = 10.26
+# 50 attoseconds in atomic time units (1 a.u. = 24.188843 as), as the configs round it.
+DT_50AS = 2.07
+
+# Fractional positions of the 8 atoms of the conventional cubic diamond cell:
+# the 4 fcc sites and the same sites shifted by (1/4, 1/4, 1/4).
+_FCC = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+DIAMOND_SITES = np.concatenate([_FCC, _FCC + 0.25])
+
+
+def diamond_supercell(reps: int) -> tuple[np.ndarray, np.ndarray]:
+    """Return (cell edge lengths in bohr, fractional atom positions) of a reps^3 supercell."""
+    reps = int(reps)
+    shifts = np.array([[i, j, k] for i in range(reps) for j in range(reps) for k in range(reps)], dtype=float)
+    frac = (DIAMOND_SITES[None, :, :] + shifts[:, None, :]).reshape(-1, 3) / reps
+    cell = np.full(3, SI_CUBIC_CELL_BOHR * reps)
+    return cell, frac
+
+
+# Named workloads: grid points per edge, supercell repetitions, orbitals.
+SI_CONFIGS = {
+    "si8": dict(n=(32, 32, 32), reps=1, n_orb=16),
+    "si64": dict(n=(64, 64, 64), reps=2, n_orb=128),
+    "si216": dict(n=(96, 96, 96), reps=3, n_orb=432),
+}
+
+# Physical parameters common to every workload (Gaussian wells of depth 2 Ha and
+# width 1.2 bohr, screened exchange with w = 0.106 / bohr and mixing 0.25, 10 Ha
+# cutoff, kick 0.01 / bohr along x, dt = 50 as).
+COMMON = dict(
+    ecut=10.0,
+    well_depth=2.0,
+    well_sigma=1.2,
+    omega=0.106,
+    alpha=0.25,
+    dt=DT_50AS,
+    kick=(0.01, 0.0, 0.0),
+    anderson_dim=20,
+    anderson_beta=1.0,
+    scf_tol=1e-6,
+    scf_max=50,
+    scf_fixed_iters=0,
+)
+
+
+def si_workload(name: str, **overrides) -> dict:
+    """Full parameter dictionary of a named silicon workload (cell, atoms, grid, physics)."""
+    cfg = SI_CONFIGS[name]
+    cell, frac = diamond_supercell(cfg["reps"])
+    out = dict(COMMON)
+    out.update(n=tuple(cfg["n"]), cell=tuple(cell), atoms=frac, n_orb=cfg["n_orb"], seed=0)
+    out.update(overrides)
+    return out
+
+
+def initial_coefficients(g2_basis: np.ndarray, n_orb: int, seed: int) -> np.ndarray:
+    """Random initial orbital coefficients, shape (n_orb, n_basis), complex128.
+
+    ``g2_basis`` is |G|^2 of each basis vector in basis order (supplied by the
+    caller). Row b is orbital b. The envelope exp(-|G|^2/4) keeps the start
+    state smooth; the rows are not orthonormal.
+    """
+    g2 = np.asarray(g2_basis, dtype=np.float64)
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    z = rng.standard_normal((int(n_orb), g2.size, 2))
+    return (z[..., 0] + 1j * z[..., 1]) * np.exp(-g2 / 4.0)[None, :]
+
+
+def batched_kicks(count: int, seed: int = 1) -> np.ndarray:
+    """Kick vectors for a batch of trajectories: axis uniform over x/y/z, size U[0.005, 0.02]."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    axes = rng.integers(0, 3, size=count)
+    mags = rng.uniform(0.005, 0.02, size=count)
+    k = np.zeros((count, 3))
+    k[np.arange(count), axes] = mags
+    return k
+
+
+def gaussian_vectors(shape, seed: int) -> np.ndarray:
+    """Plain complex standard-normal array (for operator tests on arbitrary vectors)."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    z = rng.standard_normal(tuple(shape) + (2,))
+    return z[..., 0] + 1j * z[..., 1]
