@@ -1,0 +1,159 @@
+/*
+ * pt.h -- C ABI of the GB300 library for parallel-transport Crank-Nicolson
+ * real-time TDDFT with a screened hybrid functional (arXiv:1905.01348).
+ *
+ * The library applies the Fock exchange operator of Eq. 3 by a fused
+ * pair-product / 3D FFT / kernel multiply / inverse FFT / accumulate CUDA
+ * pipeline, builds and applies its adaptively compressed (ACE) form, and runs
+ * the PT-CN step of Eq. 5 / Alg. 1 (residual of Alg. 3, per-band Anderson
+ * mixing and Cholesky orthonormalisation of Sec. 3.4) on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Cell: orthorhombic, edge lengths cell[3] (bohr); grid n[3] points, row-major
+ *   with axis 2 fastest; each n[k] must be one of 8, 12, 16, 24, 32, 48, 64, 96.
+ * Basis: the grid frequencies G = 2 pi m / a with |G|^2 / 2 <= ecut, listed
+ *   by increasing flat grid index (m in FFT index order). npw = basis size.
+ * Orbitals: complex128, interleaved (re, im), band-major: orbital b occupies
+ *   elements [b * npw, (b + 1) * npw). psi(r) = Omega^{-1/2} sum_G c(G) e^{iG.r}.
+ * Occupation: every orbital doubly occupied, rho = 2 sum_b |psi_b|^2 (spin
+ *   omitted as in Sec. 2).
+ * Memory: the caller owns all device memory. pt_init_system receives one
+ *   device workspace of at least pt_workspace_size() bytes (256-byte aligned)
+ *   and a cudaStream_t (as void*, NULL = default stream); the library never
+ *   allocates device memory and enqueues all device work on that stream.
+ *   Host pointers are borrowed for the duration of the call. The workspace
+ *   must stay valid until pt_destroy.
+ * Errors: every call returns pt_status. On failure nothing is aborted;
+ *   pt_last_error() gives a message. A failed step leaves the orbitals at the
+ *   last consistent state. Calls that return host data synchronise the stream.
+ * Threads: a pt_system is not thread safe; distinct systems are independent.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pt_status {
+  PT_OK = 0,
+  PT_ERR_INVALID = 1,        /* bad argument or unsupported size */
+  PT_ERR_OOM = 2,            /* workspace smaller than pt_workspace_size() */
+  PT_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  PT_ERR_NOT_CONVERGED = 4,  /* SCF loop reached scf_max (state still advanced) */
+  PT_ERR_NOT_PD = 5,         /* Cholesky met a non-positive pivot */
+  PT_ERR_TIMEOUT = 6         /* a bounded device wait gave up */
+} pt_status;
+
+enum { PT_FP64 = 0, PT_MIXED = 1 };                       /* precision */
+enum { PT_FOCK_EXACT = 0, PT_FOCK_ACE = 1, PT_FOCK_NONE = 2 }; /* exchange mode */
+
+typedef struct pt_params {
+  int n[3];              /* grid points per axis */
+  double cell[3];        /* cell edge lengths, bohr */
+  double ecut;           /* planewave cutoff, Ha (Sec. 4: 10 Ha) */
+  int n_orb;             /* number of orbitals N_e */
+  int n_atoms;           /* Gaussian wells */
+  const double* atom_frac; /* host, 3 * n_atoms fractional positions (read during init only) */
+  double well_depth;     /* D: V_ion(r) = -D sum_a exp(-|r - R_a|^2 / (2 sigma^2)) */
+  double well_sigma;     /* sigma, bohr */
+  double omega;          /* screening w of K(r) = erfc(w r)/r, bohr^-1 */
+  double alpha;          /* Fock mixing fraction (Sec. 2); (1 - alpha) Slater exchange */
+  double dt;             /* time step, a.u. (Sec. 4: 50 as) */
+  double kick[3];        /* velocity-gauge kick kappa, bohr^-1: kinetic |G + kappa|^2 / 2 */
+  int anderson_dim;      /* Anderson history depth (Sec. 4: 20) */
+  double anderson_beta;  /* Anderson mixing parameter */
+  double scf_tol;        /* density-change tolerance (Sec. 4: 1e-6) */
+  int scf_max;           /* iteration cap when scf_fixed_iters == 0 */
+  int scf_fixed_iters;   /* > 0: run exactly this many SCF iterations */
+  int precision;         /* PT_FP64, or PT_MIXED: FP32 pair FFTs and ACE products */
+  int fock_mode;         /* PT_FOCK_EXACT (V_X every SCF iteration) or PT_FOCK_ACE (once per step) */
+  int use_hartree;       /* 1: include the Hartree potential */
+  int use_lda;           /* 1: include (1 - alpha) Slater exchange */
+  int relax_iters;       /* start-state relaxation steps (steepest descent on H_loc) */
+  double relax_tau;      /* relaxation step length */
+  int pair_tile;         /* orbitals per pair-tile edge (0 = automatic) */
+} pt_params;
+
+typedef struct pt_system pt_system;
+
+typedef struct pt_step_info {
+  int scf_iters;         /* SCF iterations taken */
+  int converged;         /* 1 if the density change fell below scf_tol (or fixed iterations) */
+  double resid_norm;     /* Frobenius norm of R_f at the last iteration (FP64) */
+  double drho;           /* last density change dV sum |rho_new - rho_old| / (2 N_e) */
+  double energy;         /* total energy of the new orbitals, Ha */
+  double dipole[3];      /* -dV sum_r r rho(r), r in [0, a) */
+} pt_step_info;
+
+/* Basis size for these parameters. Planewave basis of Sec. 3.1 / Sec. 4. */
+pt_status pt_basis_size(const pt_params* p, int* npw);
+
+/* Basis listing: flat grid index (int64) of each basis vector, in basis order.
+ * out_host must hold npw entries. */
+pt_status pt_basis_indices(const pt_params* p, int64_t* out_host);
+
+/* Device workspace bytes pt_init_system needs for these parameters. */
+pt_status pt_workspace_size(const pt_params* p, size_t* bytes);
+
+/* Create a system (Eq. 5 state). psi0_host: n_orb x npw complex128 initial
+ * coefficients (need not be orthonormal). They are orthonormalised by
+ * Cholesky (Sec. 3.4), relaxed by relax_iters steepest-descent steps on the
+ * local Hamiltonian, and the exchange data of the start state (W = V_X Psi,
+ * and ACE when fock_mode is PT_FOCK_ACE) are built. Synchronises the stream. */
+pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_workspace,
+                         size_t workspace_bytes, void* stream, pt_system** out);
+
+/* Build ACE from the current orbitals (ACE cited in Sec. 1): W = V_X Psi by
+ * the symmetric pair pipeline (Eq. 3, Alg. 2), M = Psi^H W, -M = L L^H,
+ * xi = W L^{-H}. Returns PT_ERR_NOT_PD if -M is not positive definite. */
+pt_status pt_build_ace(pt_system* s);
+
+/* Y = H[P] X for ncols device columns X (complex128, band-major, npw each),
+ * P the current density matrix; H as in Eq. 2. fock_mode PT_FOCK_EXACT
+ * applies V_X by the pair pipeline (Eq. 3), PT_FOCK_ACE applies
+ * -xi (xi^H X), PT_FOCK_NONE omits exchange. X and Y may not overlap. */
+pt_status pt_apply_h(pt_system* s, const void* d_X, void* d_Y, int ncols, int fock_mode);
+
+/* W = V_X[P] Psi for the current orbitals, device output (npw x n_orb
+ * complex128, band-major). The hot path: symmetric pair tiles, Eq. 3. */
+pt_status pt_exchange(pt_system* s, void* d_W);
+
+/* One PT-CN step (Eq. 5, Alg. 1). out (host, may be NULL) receives the step
+ * information. Returns PT_ERR_NOT_CONVERGED if scf_max was reached (the step
+ * is still taken). */
+pt_status pt_cn_step(pt_system* s, pt_step_info* out);
+
+/* nsteps PT-CN steps; out_host (may be NULL) receives nsteps entries. Stops
+ * early only on an error other than PT_ERR_NOT_CONVERGED. */
+pt_status pt_propagate(pt_system* s, int nsteps, pt_step_info* out_host);
+
+/* Copy the current orbitals (n_orb x npw complex128) to host memory. */
+pt_status pt_get_orbitals(pt_system* s, double* psi_host);
+
+/* Replace the current orbitals (n_orb x npw complex128, host), orthonormalise
+ * them and rebuild the exchange data (no relaxation). Checkpoint resume. */
+pt_status pt_set_orbitals(pt_system* s, const double* psi_host);
+
+/* Energy and dipole of the current orbitals (host outputs, dipole[3]). */
+pt_status pt_observables(pt_system* s, double* energy, double* dipole);
+
+/* Device pointer of the current orbitals (npw x n_orb complex128). */
+pt_status pt_orbitals_device(pt_system* s, void** d_psi);
+
+/* Release the handle (the workspace stays owned by the caller). */
+pt_status pt_destroy(pt_system* s);
+
+/* Message of the last error on this handle (or of the last failed create
+ * when s is NULL). Never NULL. */
+const char* pt_last_error(const pt_system* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

@@ -1,0 +1,233 @@
+"""ctypes binding of the C ABI in include/pt.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls. All compute
+happens in libptfock.so; when that library is missing this module raises
+instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libptfock.so")
+
+PT_OK, PT_ERR_INVALID, PT_ERR_OOM, PT_ERR_CUDA, PT_ERR_NOT_CONVERGED, PT_ERR_NOT_PD, PT_ERR_TIMEOUT = range(7)
+PT_FP64, PT_MIXED = 0, 1
+PT_FOCK_EXACT, PT_FOCK_ACE, PT_FOCK_NONE = 0, 1, 2
+STATUS_NAMES = {0: "PT_OK", 1: "PT_ERR_INVALID", 2: "PT_ERR_OOM", 3: "PT_ERR_CUDA", 4: "PT_ERR_NOT_CONVERGED",
+                5: "PT_ERR_NOT_PD", 6: "PT_ERR_TIMEOUT"}
+
+
+class PtParams(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3),
+        ("cell", C.c_double * 3),
+        ("ecut", C.c_double),
+        ("n_orb", C.c_int),
+        ("n_atoms", C.c_int),
+        ("atom_frac", C.POINTER(C.c_double)),
+        ("well_depth", C.c_double),
+        ("well_sigma", C.c_double),
+        ("omega", C.c_double),
+        ("alpha", C.c_double),
+        ("dt", C.c_double),
+        ("kick", C.c_double * 3),
+        ("anderson_dim", C.c_int),
+        ("anderson_beta", C.c_double),
+        ("scf_tol", C.c_double),
+        ("scf_max", C.c_int),
+        ("scf_fixed_iters", C.c_int),
+        ("precision", C.c_int),
+        ("fock_mode", C.c_int),
+        ("use_hartree", C.c_int),
+        ("use_lda", C.c_int),
+        ("relax_iters", C.c_int),
+        ("relax_tau", C.c_double),
+        ("pair_tile", C.c_int),
+    ]
+
+
+class PtStepInfo(C.Structure):
+    _fields_ = [
+        ("scf_iters", C.c_int),
+        ("converged", C.c_int),
+        ("resid_norm", C.c_double),
+        ("drho", C.c_double),
+        ("energy", C.c_double),
+        ("dipole", C.c_double * 3),
+    ]
+
+    def as_dict(self) -> dict:
+        return dict(scf_iters=self.scf_iters, converged=bool(self.converged), resid_norm=self.resid_norm,
+                    drho=self.drho, energy=self.energy, dipole=np.array(self.dipole[:]))
+
+
+class PtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libptfock.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1905_01348_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER(PtParams)
+    vp = C.c_void_p
+    sig = {
+        "pt_basis_size": (C.c_int, [P, C.POINTER(C.c_int)]),
+        "pt_basis_indices": (C.c_int, [P, C.POINTER(C.c_int64)]),
+        "pt_workspace_size": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+        "pt_init_system": (C.c_int, [P, C.POINTER(C.c_double), vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "pt_build_ace": (C.c_int, [vp]),
+        "pt_apply_h": (C.c_int, [vp, vp, vp, C.c_int, C.c_int]),
+        "pt_exchange": (C.c_int, [vp, vp]),
+        "pt_cn_step": (C.c_int, [vp, C.POINTER(PtStepInfo)]),
+        "pt_propagate": (C.c_int, [vp, C.c_int, C.POINTER(PtStepInfo)]),
+        "pt_get_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
+        "pt_set_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
+        "pt_observables": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "pt_orbitals_device": (C.c_int, [vp, C.POINTER(vp)]),
+        "pt_destroy": (C.c_int, [vp]),
+        "pt_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, handle=None, allow=()):
+    if st != PT_OK and st not in allow:
+        raise PtError(st, pt_last_error(handle))
+    return st
+
+
+def make_params(d: dict) -> PtParams:
+    """pt_params from a workload dictionary (keys as in synthetic.si_workload)."""
+    p = PtParams()
+    for k in range(3):
+        p.n[k] = int(d["n"][k])
+        p.cell[k] = float(d["cell"][k])
+        p.kick[k] = float(d.get("kick", (0.0, 0.0, 0.0))[k])
+    p.ecut = float(d["ecut"])
+    p.n_orb = int(d["n_orb"])
+    atoms = np.ascontiguousarray(np.asarray(d.get("atoms", np.zeros((0, 3))), dtype=np.float64).reshape(-1, 3))
+    p.n_atoms = atoms.shape[0]
+    p._atoms_keepalive = atoms
+    p.atom_frac = atoms.ctypes.data_as(C.POINTER(C.c_double)) if atoms.size else None
+    p.well_depth = float(d.get("well_depth", 2.0))
+    p.well_sigma = float(d.get("well_sigma", 1.2))
+    p.omega = float(d.get("omega", 0.106))
+    p.alpha = float(d.get("alpha", 0.25))
+    p.dt = float(d.get("dt", 2.07))
+    p.anderson_dim = int(d.get("anderson_dim", 20))
+    p.anderson_beta = float(d.get("anderson_beta", 1.0))
+    p.scf_tol = float(d.get("scf_tol", 1e-6))
+    p.scf_max = int(d.get("scf_max", 50))
+    p.scf_fixed_iters = int(d.get("scf_fixed_iters", 0))
+    prec = d.get("precision", "fp64")
+    p.precision = PT_MIXED if prec in ("mixed", PT_MIXED) else PT_FP64
+    fm = d.get("fock_mode", "ace")
+    p.fock_mode = {"exact": PT_FOCK_EXACT, "ace": PT_FOCK_ACE}.get(fm, fm)
+    p.use_hartree = int(bool(d.get("use_hartree", True)))
+    p.use_lda = int(bool(d.get("use_lda", True)))
+    p.relax_iters = int(d.get("relax_iters", 40))
+    p.relax_tau = float(d.get("relax_tau", 1.0))
+    p.pair_tile = int(d.get("pair_tile", 0))
+    return p
+
+
+def pt_last_error(handle=None) -> str:
+    msg = load().pt_last_error(handle)
+    return msg.decode() if msg else ""
+
+
+def pt_basis_size(params: PtParams) -> int:
+    n = C.c_int(0)
+    _check(load().pt_basis_size(C.byref(params), C.byref(n)))
+    return n.value
+
+
+def pt_basis_indices(params: PtParams) -> np.ndarray:
+    out = np.zeros(pt_basis_size(params), dtype=np.int64)
+    _check(load().pt_basis_indices(C.byref(params), out.ctypes.data_as(C.POINTER(C.c_int64))))
+    return out
+
+
+def pt_workspace_size(params: PtParams) -> int:
+    n = C.c_size_t(0)
+    _check(load().pt_workspace_size(C.byref(params), C.byref(n)))
+    return n.value
+
+
+def pt_init_system(params: PtParams, psi0: np.ndarray, d_workspace: int, workspace_bytes: int, stream: int = 0):
+    psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    h = C.c_void_p()
+    _check(load().pt_init_system(C.byref(params), psi0.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(d_workspace),
+                                 C.c_size_t(workspace_bytes), C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def pt_build_ace(h) -> None:
+    _check(load().pt_build_ace(h), h)
+
+
+def pt_apply_h(h, d_X: int, d_Y: int, ncols: int, fock_mode: int) -> None:
+    _check(load().pt_apply_h(h, C.c_void_p(d_X), C.c_void_p(d_Y), int(ncols), int(fock_mode)), h)
+
+
+def pt_exchange(h, d_W: int) -> None:
+    _check(load().pt_exchange(h, C.c_void_p(d_W)), h)
+
+
+def pt_cn_step(h) -> tuple[int, dict]:
+    info = PtStepInfo()
+    st = _check(load().pt_cn_step(h, C.byref(info)), h, allow=(PT_ERR_NOT_CONVERGED,))
+    return st, info.as_dict()
+
+
+def pt_propagate(h, nsteps: int) -> tuple[int, list]:
+    infos = (PtStepInfo * max(1, nsteps))()
+    st = _check(load().pt_propagate(h, int(nsteps), infos), h, allow=(PT_ERR_NOT_CONVERGED,))
+    return st, [infos[k].as_dict() for k in range(nsteps)]
+
+
+def pt_get_orbitals(h, n_orb: int, npw: int) -> np.ndarray:
+    out = np.zeros((n_orb, npw), dtype=np.complex128)
+    _check(load().pt_get_orbitals(h, out.ctypes.data_as(C.POINTER(C.c_double))), h)
+    return out
+
+
+def pt_set_orbitals(h, psi: np.ndarray) -> None:
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    _check(load().pt_set_orbitals(h, psi.ctypes.data_as(C.POINTER(C.c_double))), h)
+
+
+def pt_observables(h) -> tuple[float, np.ndarray]:
+    e = C.c_double(0.0)
+    d = (C.c_double * 3)()
+    _check(load().pt_observables(h, C.byref(e), d), h)
+    return e.value, np.array(d[:])
+
+
+def pt_orbitals_device(h) -> int:
+    p = C.c_void_p()
+    _check(load().pt_orbitals_device(h, C.byref(p)), h)
+    return p.value
+
+
+def pt_destroy(h) -> None:
+    load().pt_destroy(h)

@@ -1,0 +1,855 @@
+// Engine and C ABI (include/pt.h): one PT-CN system on one GPU.
+//
+// The engine lays the caller's workspace out once (orbitals and their
+// Anderson history in the planewave basis, real-space orbitals and exchange
+// accumulators, the pair intermediate, tables), then drives the kernels for
+//   * the exchange operator V_X Psi (Eq. 3, pair pipeline of fock.cu),
+//   * ACE: M = Psi^H W, -M = L L^H, xi = W L^{-H}, K_ACE X = -xi (xi^H X),
+//   * H Psi (Eq. 2): kinetic diagonal, local potential by FFT, exchange,
+//   * the PT-CN step of Eq. 5 / Alg. 1 with the residual of Alg. 3,
+//     per-band Anderson mixing and Cholesky orthonormalisation (Sec. 3.4).
+// All device work is enqueued on the caller's stream; host synchronisation
+// happens only where a scalar decides control flow (SCF exit, pivots).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "pt.h"
+#include "common.cuh"
+#include "internal.h"
+#include "kernels.h"
+#include "fft.cuh"
+
+using pt::Grid3;
+
+namespace {
+
+struct Carver {
+  uintptr_t base;
+  size_t off = 0;
+  template <typename T> T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+constexpr double kSlater = 0.75;   // times (3/pi)^{1/3}
+
+}  // namespace
+
+struct pt_system {
+  pt_params p{};
+  std::vector<double> atoms;
+  std::string err;
+  cudaStream_t s = nullptr;
+  Grid3 g{};
+  long N = 0;
+  int npw = 0, ne = 0, mdim = 0, hb = 1;
+  double vol = 0.0, dV = 0.0;
+  bool mixed = false;
+  // device data
+  int* basis = nullptr;
+  double* kin = nullptr;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double* khat64 = nullptr;
+  float* khat32 = nullptr;
+  double *hfac = nullptr, *vion = nullptr, *vloc = nullptr, *vh = nullptr, *rho = nullptr, *rho2 = nullptr;
+  double* d_atoms = nullptr;
+  double2 *psi = nullptr, *psi_half = nullptr, *psi_f = nullptr, *hpsi = nullptr, *tmp = nullptr, *rbuf = nullptr;
+  double2 *wg = nullptr, *xi = nullptr, *xprev = nullptr, *rprev = nullptr, *dX = nullptr, *dR = nullptr;
+  double2* hbuf = nullptr;
+  double2* psi_r = nullptr;
+  float2* psi_r32 = nullptr;
+  void *w_r = nullptr, *x_r = nullptr, *scratch = nullptr;
+  double2 *S = nullptr, *Mneg = nullptr, *Linv = nullptr, *Z = nullptr, *gemm_ws = nullptr;
+  size_t gemm_ws_elems = 0;
+  double2 *gram = nullptr, *rhs = nullptr, *gamma = nullptr;
+  double *part = nullptr, *red = nullptr;
+  int* status = nullptr;
+  pt::PairTile *d_tiles_sym = nullptr, *d_tiles_x = nullptr;
+  size_t max_tiles_x = 0;
+  pt::FockPlan plan_sym{}, plan_x{};
+  int plan_x_ncols = -1;
+  pt::DevTwiddles tw{};
+  // host state
+  bool have_ace = false;
+  bool psi_r_current = false;   // psi_r holds the real-space form of psi
+  double energy = 0.0, dipole[3] = {0, 0, 0};
+  int and_count = 0;
+  std::vector<int> and_order;
+};
+
+static std::string g_last_error = "no error";
+
+#define PT_CK(call)                                                               \
+  do {                                                                            \
+    cudaError_t _e = (call);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      sys->err = std::string(#call) + " -> " + pt::cuda_msg(_e);                  \
+      return PT_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+#define PT_TRY(call)                        \
+  do {                                      \
+    pt_status _st = (call);                 \
+    if (_st != PT_OK) return _st;           \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// parameter checks and host tables
+
+static bool supported_n(int n) { return pt::fft_length_supported(n); }
+
+static pt_status check_params(const pt_params* p, std::string* why) {
+  if (p == nullptr) { *why = "params is NULL"; return PT_ERR_INVALID; }
+  for (int k = 0; k < 3; ++k) {
+    if (!supported_n(p->n[k])) { *why = "grid size must be one of 8,12,16,24,32,48,64,96"; return PT_ERR_INVALID; }
+    if (!(p->cell[k] > 0.0)) { *why = "cell lengths must be positive"; return PT_ERR_INVALID; }
+  }
+  if (!(p->ecut > 0.0)) { *why = "ecut must be positive"; return PT_ERR_INVALID; }
+  if (p->n_orb < 1) { *why = "n_orb must be >= 1"; return PT_ERR_INVALID; }
+  if (p->n_atoms < 0 || (p->n_atoms > 0 && p->atom_frac == nullptr)) { *why = "atoms"; return PT_ERR_INVALID; }
+  if (p->anderson_dim < 0 || p->anderson_dim > 20) { *why = "anderson_dim must be in [0, 20]"; return PT_ERR_INVALID; }
+  if (p->precision != PT_FP64 && p->precision != PT_MIXED) { *why = "precision"; return PT_ERR_INVALID; }
+  if (p->fock_mode != PT_FOCK_EXACT && p->fock_mode != PT_FOCK_ACE) { *why = "fock_mode"; return PT_ERR_INVALID; }
+  if (!(p->omega > 0.0)) { *why = "omega must be positive"; return PT_ERR_INVALID; }
+  if (p->pair_tile < 0 || p->pair_tile > pt::kTileMax) { *why = "pair_tile must be in [0, 4]"; return PT_ERR_INVALID; }
+  if (p->scf_max < 1 && p->scf_fixed_iters < 1) { *why = "scf_max or scf_fixed_iters must be >= 1"; return PT_ERR_INVALID; }
+  return PT_OK;
+}
+
+static inline int freq(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+
+static void basis_list(const pt_params* p, std::vector<int>* idx, std::vector<double>* g2out) {
+  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+  idx->clear();
+  if (g2out) g2out->clear();
+  for (int i0 = 0; i0 < n0; ++i0)
+    for (int i1 = 0; i1 < n1; ++i1)
+      for (int i2 = 0; i2 < n2; ++i2) {
+        const double g0 = 2.0 * M_PI * freq(i0, n0) / p->cell[0];
+        const double g1 = 2.0 * M_PI * freq(i1, n1) / p->cell[1];
+        const double g2 = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
+        const double gg = g0 * g0 + g1 * g1 + g2 * g2;
+        if (0.5 * gg <= p->ecut) {
+          idx->push_back((i0 * n1 + i1) * n2 + i2);
+          if (g2out) g2out->push_back(gg);
+        }
+      }
+}
+
+static int choose_tile(const pt_params* p) {
+  if (p->pair_tile > 0) return p->pair_tile;
+  return std::min(pt::kTileMax, p->n_orb);
+}
+
+static int tiles_per_launch(const pt_params* p, long N, bool mixed) {
+  const int tile = choose_tile(p);
+  const int nb = (p->n_orb + tile - 1) / tile;
+  const double per_tile = (double)pt::kTileMax * pt::kTileMax * N * (mixed ? 8.0 : 16.0);
+  const double budget = 16.0e9;
+  int cap = (int)std::max(1.0, std::floor(budget / per_tile));
+  return std::max(1, std::min(nb, cap));
+}
+
+static int h_batch(const pt_params* p) { return std::min(p->n_orb, 32); }
+
+// Carve (or size, when base == 0) the workspace.
+static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
+  Carver c{base};
+  std::vector<int> idx;
+  basis_list(p, &idx, nullptr);
+  const long npw = (long)idx.size();
+  const long N = (long)p->n[0] * p->n[1] * p->n[2];
+  const long ne = p->n_orb;
+  const int m = p->anderson_dim;
+  const bool mixed = p->precision == PT_MIXED;
+  const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
+  const int tile = choose_tile(p);
+  const long nb = (ne + tile - 1) / tile;
+  const int tpl = tiles_per_launch(p, N, mixed);
+  const int hb = h_batch(p);
+  pt_system dummy;
+  pt_system* t = sys ? sys : &dummy;
+  t->basis = c.take<int>(npw);
+  t->kin = c.take<double>(npw);
+  t->tw64 = c.take<double2>(pt::kTwiddleTotal);
+  t->tw32 = c.take<float2>(pt::kTwiddleTotal);
+  if (mixed) t->khat32 = c.take<float>(N); else t->khat64 = c.take<double>(N);
+  t->hfac = c.take<double>(N);
+  t->vion = c.take<double>(N);
+  t->vloc = c.take<double>(N);
+  t->vh = c.take<double>(N);
+  t->rho = c.take<double>(N);
+  t->rho2 = c.take<double>(N);
+  t->d_atoms = c.take<double>(3 * std::max(1, p->n_atoms));
+  const size_t pe = (size_t)npw * ne;
+  t->psi = c.take<double2>(pe);
+  t->psi_half = c.take<double2>(pe);
+  t->psi_f = c.take<double2>(pe);
+  t->hpsi = c.take<double2>(pe);
+  t->tmp = c.take<double2>(pe);
+  t->rbuf = c.take<double2>(pe);
+  t->wg = c.take<double2>(pe);
+  t->xi = c.take<double2>(pe);
+  t->xprev = c.take<double2>(pe);
+  t->rprev = c.take<double2>(pe);
+  t->dX = c.take<double2>(pe * std::max(1, m));
+  t->dR = c.take<double2>(pe * std::max(1, m));
+  t->hbuf = c.take<double2>((size_t)N * hb);
+  t->psi_r = c.take<double2>((size_t)N * ne);
+  if (mixed) t->psi_r32 = c.take<float2>((size_t)N * ne);
+  t->w_r = c.take<unsigned char>((size_t)N * ne * cs);
+  t->x_r = c.take<unsigned char>((size_t)N * ne * cs);
+  t->scratch = c.take<unsigned char>((size_t)tpl * pt::kTileMax * pt::kTileMax * N * cs);
+  t->S = c.take<double2>(ne * ne);
+  t->Mneg = c.take<double2>(ne * ne);
+  t->Linv = c.take<double2>(ne * ne);
+  t->Z = c.take<double2>(ne * ne);
+  t->gemm_ws_elems = (size_t)16 * ne * ne + 4096;
+  t->gemm_ws = c.take<double2>(t->gemm_ws_elems);
+  t->gram = c.take<double2>((size_t)ne * std::max(1, m) * std::max(1, m));
+  t->rhs = c.take<double2>((size_t)ne * std::max(1, m));
+  t->gamma = c.take<double2>((size_t)ne * std::max(1, m));
+  t->part = c.take<double>(8192);
+  t->red = c.take<double>(64);
+  t->status = c.take<int>(16);
+  t->d_tiles_sym = c.take<pt::PairTile>((size_t)(nb * (nb - 1) / 2 + nb));
+  t->max_tiles_x = (size_t)nb * nb;
+  t->d_tiles_x = c.take<pt::PairTile>(t->max_tiles_x);
+  return c.off + 256;
+}
+
+// ---------------------------------------------------------------------------
+// building blocks
+
+template <typename T>
+static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst) {
+  PT_CK(pt::scatter_basis<T>(c, sys->npw, dst, ncols, sys->g, sys->basis, sys->npw, 1.0 / std::sqrt(sys->vol), sys->s));
+  PT_CK(pt::fft_rows<T>(dst, dst, ncols, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(dst, ncols, sys->g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(dst, ncols, sys->g, 0, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+  return PT_OK;
+}
+
+// forward transform of src (destroyed) and gather into out (scale sqrt(Omega)/N)
+template <typename T>
+static pt_status to_basis(pt_system* sys, void* src, long ncols, double2* out, int accumulate, const double* kin,
+                          const double2* x) {
+  PT_CK(pt::fft_rows<T>(src, src, ncols, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(src, ncols, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(src, ncols, sys->g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::gather_basis<T>(src, out, sys->npw, ncols, sys->g, sys->basis, sys->npw, std::sqrt(sys->vol) / sys->N, kin,
+                            x, sys->npw, accumulate, sys->s));
+  return PT_OK;
+}
+
+// psi_r (and its FP32 copy) <- real-space form of the columns c (n_orb of them)
+static pt_status real_orbitals(pt_system* sys, const double2* c) {
+  PT_TRY(to_real<double>(sys, c, sys->ne, sys->psi_r));
+  if (sys->mixed) PT_CK(pt::convert_c128_to_c64(sys->psi_r, sys->psi_r32, sys->N * sys->ne, sys->s));
+  return PT_OK;
+}
+
+static pt_status local_potential(pt_system* sys) {
+  const int use_h = sys->p.use_hartree ? 1 : 0;
+  if (use_h) {
+    PT_CK(pt::rho_to_complex(sys->rho, sys->hbuf, sys->N, sys->s));
+    PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, 1, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 0, 0, 2, 1.0, sys->hfac, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, 1, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
+  }
+  const double w_lda = sys->p.use_lda ? (1.0 - sys->p.alpha) : 0.0;
+  PT_CK(pt::assemble_vloc(sys->vion, sys->hbuf, sys->rho, sys->N, use_h, w_lda, sys->vh, sys->vloc, sys->s));
+  return PT_OK;
+}
+
+// out = kin * c + local(vloc) c, using the real-space form psi_r of the n_orb columns c
+static pt_status apply_local_from_real(pt_system* sys, const double2* c, double2* out) {
+  for (int c0 = 0; c0 < sys->ne; c0 += sys->hb) {
+    const int cnt = std::min(sys->hb, sys->ne - c0);
+    PT_CK(pt::fft_rows<double>(sys->psi_r + (long)c0 * sys->N, sys->hbuf, cnt, sys->g, 0, 1.0, sys->vloc, sys->tw,
+                               sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, cnt, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, cnt, sys->g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::gather_basis<double>(sys->hbuf, out + (long)c0 * sys->npw, sys->npw, cnt, sys->g, sys->basis, sys->npw,
+                                   std::sqrt(sys->vol) / sys->N, sys->kin, c + (long)c0 * sys->npw, sys->npw, 0,
+                                   sys->s));
+  }
+  return PT_OK;
+}
+
+// out = kin * X + local(vloc) X for arbitrary columns X
+static pt_status apply_local(pt_system* sys, const double2* X, double2* out, int ncols) {
+  for (int c0 = 0; c0 < ncols; c0 += sys->hb) {
+    const int cnt = std::min(sys->hb, ncols - c0);
+    PT_CK(pt::scatter_basis<double>(X + (long)c0 * sys->npw, sys->npw, sys->hbuf, cnt, sys->g, sys->basis, sys->npw,
+                                    1.0 / std::sqrt(sys->vol), sys->s));
+    PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, cnt, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, cnt, sys->g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, cnt, sys->g, 0, 1, 1, 1.0, sys->vloc, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<double>(sys->hbuf, cnt, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, cnt, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::gather_basis<double>(sys->hbuf, out + (long)c0 * sys->npw, sys->npw, cnt, sys->g, sys->basis, sys->npw,
+                                   std::sqrt(sys->vol) / sys->N, sys->kin, X + (long)c0 * sys->npw, sys->npw, 0,
+                                   sys->s));
+  }
+  return PT_OK;
+}
+
+// V_X Psi for the orbitals whose real-space form is in psi_r; out = (or +=) result
+template <typename T>
+static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
+  const size_t cs = sizeof(pt::cplx<T>);
+  PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * sys->N * sys->ne, sys->s));
+  const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
+  const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
+  PT_CK(pt::fock_pairs<T>(pr, nullptr, sys->w_r, nullptr, sys->plan_sym, 1, sys->g, kt, sys->scratch, sys->tw, sys->s));
+  return to_basis<T>(sys, sys->w_r, sys->ne, out, accumulate, nullptr, nullptr);
+}
+
+static pt_status exchange_sym(pt_system* sys, double2* out, int accumulate) {
+  if (sys->p.alpha == 0.0) {
+    if (!accumulate) PT_CK(cudaMemsetAsync(out, 0, sizeof(double2) * sys->npw * sys->ne, sys->s));
+    return PT_OK;
+  }
+  return sys->mixed ? exchange_sym_t<float>(sys, out, accumulate) : exchange_sym_t<double>(sys, out, accumulate);
+}
+
+static pt_status ensure_plan_x(pt_system* sys, int ncols) {
+  if (sys->plan_x_ncols == ncols) return PT_OK;
+  pt::PairTile* tiles = nullptr;
+  int *lf = nullptr, *lc = nullptr, nl = 0;
+  const int tile = choose_tile(&sys->p);
+  const int nt = pt::fock_build_tiles(sys->ne, ncols, tile, 0, tiles_per_launch(&sys->p, sys->N, sys->mixed), &tiles,
+                                      &lf, &lc, &nl);
+  if (nt < 0 || (size_t)nt > sys->max_tiles_x) {
+    std::free(tiles); std::free(lf); std::free(lc);
+    sys->err = "exchange tile schedule does not fit";
+    return PT_ERR_INVALID;
+  }
+  PT_CK(cudaMemcpyAsync(sys->d_tiles_x, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  std::free(tiles);
+  std::free(sys->plan_x.launch_first);
+  std::free(sys->plan_x.launch_count);
+  sys->plan_x.tile = tile;
+  sys->plan_x.tiles_per_launch = tiles_per_launch(&sys->p, sys->N, sys->mixed);
+  sys->plan_x.n_launch = nl;
+  sys->plan_x.launch_first = lf;
+  sys->plan_x.launch_count = lc;
+  sys->plan_x.d_tiles = sys->d_tiles_x;
+  sys->plan_x.n_tiles = nt;
+  sys->plan_x_ncols = ncols;
+  return PT_OK;
+}
+
+template <typename T>
+static pt_status exchange_x_t(pt_system* sys, const double2* X, int ncols, double2* out) {
+  const size_t cs = sizeof(pt::cplx<T>);
+  PT_TRY(ensure_plan_x(sys, ncols));
+  PT_TRY(to_real<T>(sys, X, ncols, sys->x_r));
+  PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * sys->N * ncols, sys->s));
+  const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
+  const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
+  PT_CK(pt::fock_pairs<T>(pr, sys->x_r, nullptr, sys->w_r, sys->plan_x, 0, sys->g, kt, sys->scratch, sys->tw, sys->s));
+  return to_basis<T>(sys, sys->w_r, ncols, out, 1, nullptr, nullptr);
+}
+
+template <typename Tc>
+static pt_status gemm(pt_system* sys, int opA, int opB, int M, int N, int K, double2 alpha, const double2* A, long lda,
+                      const double2* B, long ldb, double2 beta, double2* C, long ldc) {
+  PT_CK(pt::gemm<Tc>(opA, opB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1, sys->gemm_ws,
+                     sys->gemm_ws_elems, sys->s));
+  return PT_OK;
+}
+
+static const double2 kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMinusOne = {-1.0, 0.0};
+
+static pt_status read_status(pt_system* sys, int* h) {
+  PT_CK(cudaMemcpyAsync(h, sys->status, sizeof(int), cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+// dst = src L^{-H}, L L^H = src^H src  (Sec. 3.4)
+static pt_status orthonormalize(pt_system* sys, const double2* src, double2* dst) {
+  const int ne = sys->ne, npw = sys->npw;
+  PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, src, npw, src, npw, kZero, sys->S, ne));
+  PT_CK(pt::cholesky(sys->S, ne, sys->status, sys->s));
+  int h = 0;
+  PT_TRY(read_status(sys, &h));
+  if (h != 0) { sys->err = "orthonormalisation: overlap matrix is not positive definite"; return PT_ERR_NOT_PD; }
+  PT_CK(pt::tri_inverse(sys->S, sys->Linv, ne, sys->s));
+  PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, src, npw, sys->Linv, ne, kZero, dst, npw));
+  return PT_OK;
+}
+
+// exchange data of psi (psi_r current): wg = V_X psi, Mneg = -psi^H wg, ACE
+static pt_status exchange_data(pt_system* sys) {
+  const int ne = sys->ne, npw = sys->npw;
+  PT_TRY(exchange_sym(sys, sys->wg, 0));
+  const bool ace = sys->p.fock_mode == PT_FOCK_ACE && sys->p.alpha != 0.0;
+  if (sys->mixed && ace)
+    PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kMinusOne, sys->psi, npw, sys->wg, npw, kZero, sys->Mneg, ne));
+  else
+    PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kMinusOne, sys->psi, npw, sys->wg, npw, kZero, sys->Mneg, ne));
+  sys->have_ace = false;
+  if (!ace) return PT_OK;
+  PT_CK(cudaMemcpyAsync(sys->S, sys->Mneg, sizeof(double2) * ne * ne, cudaMemcpyDeviceToDevice, sys->s));
+  PT_CK(pt::cholesky(sys->S, ne, sys->status, sys->s));
+  int h = 0;
+  PT_TRY(read_status(sys, &h));
+  if (h != 0) { sys->err = "ACE: -M is not positive definite"; return PT_ERR_NOT_PD; }
+  PT_CK(pt::tri_inverse(sys->S, sys->Linv, ne, sys->s));
+  if (sys->mixed)
+    PT_TRY(gemm<float>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->wg, npw, sys->Linv, ne, kZero, sys->xi, npw));
+  else
+    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->wg, npw, sys->Linv, ne, kZero, sys->xi, npw));
+  sys->have_ace = true;
+  return PT_OK;
+}
+
+// out += -xi (xi^H X)
+static pt_status ace_apply(pt_system* sys, const double2* X, int ncols, double2* out) {
+  const int ne = sys->ne, npw = sys->npw;
+  if (sys->mixed) {
+    PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ncols, npw, kOne, sys->xi, npw, X, npw, kZero, sys->Z, ne));
+    PT_TRY(gemm<float>(sys, pt::OP_N, pt::OP_N, npw, ncols, ne, kMinusOne, sys->xi, npw, sys->Z, ne, kOne, out, npw));
+  } else {
+    PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ncols, npw, kOne, sys->xi, npw, X, npw, kZero, sys->Z, ne));
+    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ncols, ne, kMinusOne, sys->xi, npw, sys->Z, ne, kOne, out, npw));
+  }
+  return PT_OK;
+}
+
+// energy and dipole of psi (psi_r current, Mneg current)
+static pt_status observables(pt_system* sys) {
+  PT_CK(pt::density(sys->psi_r, sys->N, sys->ne, sys->rho, sys->s));
+  PT_TRY(local_potential(sys));
+  PT_CK(pt::energy_sums(sys->rho, sys->vion, sys->vh, sys->p.use_hartree ? 1 : 0, sys->g, sys->p.cell, sys->psi,
+                        sys->kin, sys->npw, sys->ne, sys->Mneg, sys->part, sys->red + 8, sys->s));
+  double h[8];
+  PT_CK(cudaMemcpyAsync(h, sys->red + 8, sizeof(h), cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  const double dV = sys->dV;
+  double e = 2.0 * h[6] + dV * h[0];
+  if (sys->p.use_hartree) e += 0.5 * dV * h[1];
+  if (sys->p.use_lda) e += (1.0 - sys->p.alpha) * (-kSlater * std::cbrt(3.0 / M_PI)) * dV * h[2];
+  e += -h[7];
+  sys->energy = e;
+  for (int k = 0; k < 3; ++k) sys->dipole[k] = -dV * h[3 + k];
+  return PT_OK;
+}
+
+// relaxation of the start state: psi <- orth(psi - tau P (H_loc psi - psi S))
+static pt_status relax(pt_system* sys) {
+  const int ne = sys->ne, npw = sys->npw;
+  const long n = (long)npw * ne;
+  for (int k = 0; k < sys->p.relax_iters; ++k) {
+    PT_TRY(real_orbitals(sys, sys->psi));
+    PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho, sys->s));
+    PT_TRY(local_potential(sys));
+    PT_TRY(apply_local_from_real(sys, sys->psi, sys->hpsi));
+    PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->psi, npw, sys->hpsi, npw, kZero, sys->S, ne));
+    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->psi, npw, sys->S, ne, kOne, sys->hpsi, npw));
+    PT_CK(pt::precond_step(sys->psi, sys->hpsi, sys->kin, npw, n, sys->p.relax_tau, sys->s));
+    PT_TRY(orthonormalize(sys, sys->psi, sys->psi_f));
+    std::swap(sys->psi, sys->psi_f);
+  }
+  return PT_OK;
+}
+
+static pt_status state_from_psi(pt_system* sys) {
+  PT_TRY(real_orbitals(sys, sys->psi));
+  sys->psi_r_current = true;
+  PT_TRY(exchange_data(sys));
+  PT_TRY(observables(sys));
+  return PT_OK;
+}
+
+// one PT-CN step (Eq. 5, Alg. 1)
+static pt_status cn_step(pt_system* sys, pt_step_info* info) {
+  const int ne = sys->ne, npw = sys->npw;
+  const long n = (long)npw * ne;
+  const double hdt = 0.5 * sys->p.dt;
+  const int m = sys->p.anderson_dim;
+  const long stride = n;
+  if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
+  // initial residual R_n = H_n Psi_n - Psi_n (Psi_n^H H_n Psi_n) and the half step
+  PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho, sys->s));
+  PT_TRY(local_potential(sys));
+  PT_TRY(apply_local_from_real(sys, sys->psi, sys->hpsi));
+  PT_CK(pt::axpy(kOne, sys->wg, sys->hpsi, n, sys->s));
+  PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->psi, npw, sys->hpsi, npw, kZero, sys->S, ne));
+  PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->psi, npw, sys->S, ne, kOne, sys->hpsi, npw));
+  PT_CK(pt::half_step(sys->psi, sys->hpsi, hdt, sys->psi_half, n, sys->s));
+  PT_CK(cudaMemcpyAsync(sys->psi_f, sys->psi_half, sizeof(double2) * n, cudaMemcpyDeviceToDevice, sys->s));
+  PT_TRY(real_orbitals(sys, sys->psi_f));
+  sys->psi_r_current = false;
+  PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho, sys->s));
+  // SCF loop
+  const int fixed = sys->p.scf_fixed_iters;
+  const int niter = fixed > 0 ? fixed : sys->p.scf_max;
+  sys->and_count = 0;
+  sys->and_order.clear();
+  bool have_prev = false;
+  bool converged = false;
+  int it = 0;
+  double drho = 0.0;
+  for (it = 1; it <= niter; ++it) {
+    PT_TRY(local_potential(sys));
+    PT_TRY(apply_local_from_real(sys, sys->psi_f, sys->hpsi));
+    if (sys->p.alpha != 0.0) {
+      if (sys->p.fock_mode == PT_FOCK_EXACT) PT_TRY(exchange_sym(sys, sys->hpsi, 1));
+      else PT_TRY(ace_apply(sys, sys->psi_f, ne, sys->hpsi));
+    }
+    PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->psi_f, npw, sys->hpsi, npw, kZero, sys->S, ne));
+    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->psi_f, npw, sys->S, ne, kOne, sys->hpsi,
+                        npw));
+    PT_CK(pt::pt_residual(sys->psi_f, sys->hpsi, sys->psi_half, hdt, sys->rbuf, n, sys->part, sys->red + 0, sys->s));
+    // Anderson (per band)
+    int newslot = -1;
+    if (have_prev && m > 0) {
+      if (sys->and_count < m) {
+        newslot = sys->and_count;
+        sys->and_count++;
+      } else {
+        newslot = sys->and_order.front();
+        sys->and_order.erase(sys->and_order.begin());
+      }
+      sys->and_order.push_back(newslot);
+    }
+    PT_CK(pt::anderson_push(sys->psi_f, sys->rbuf, sys->xprev, sys->rprev,
+                            sys->dX + (newslot >= 0 ? newslot : 0) * stride,
+                            sys->dR + (newslot >= 0 ? newslot : 0) * stride, n, newslot >= 0 ? 1 : 0, sys->s));
+    have_prev = true;
+    pt::SlotList sl{};
+    sl.k = (int)sys->and_order.size();
+    for (int q = 0; q < sl.k; ++q) sl.s[q] = sys->and_order[q];
+    if (sl.k > 0) {
+      PT_CK(pt::anderson_dots(sys->dR, stride, sl, newslot, sys->rbuf, npw, ne, m, sys->gram, sys->rhs, sys->s));
+      PT_CK(pt::anderson_solve(sys->gram, sys->rhs, sl, m, ne, sys->gamma, sys->s));
+    }
+    PT_CK(pt::anderson_update(sys->psi_f, sys->rbuf, sys->dX, sys->dR, stride, sl, sys->gamma, std::max(m, 1), npw, n,
+                              sys->p.anderson_beta, sys->s));
+    // new density and its change
+    PT_TRY(real_orbitals(sys, sys->psi_f));
+    PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho2, sys->s));
+    PT_CK(pt::rho_change(sys->rho2, sys->rho, sys->N, sys->part, sys->red + 1, sys->s));
+    std::swap(sys->rho, sys->rho2);
+    if (fixed == 0) {
+      double h = 0.0;
+      PT_CK(cudaMemcpyAsync(&h, sys->red + 1, sizeof(double), cudaMemcpyDeviceToHost, sys->s));
+      PT_CK(cudaStreamSynchronize(sys->s));
+      drho = h * sys->dV / (2.0 * ne);
+      if (drho < sys->p.scf_tol) { converged = true; break; }
+    }
+  }
+  if (it > niter) it = niter;
+  if (fixed > 0) converged = true;
+  double hres[2];
+  PT_CK(cudaMemcpyAsync(hres, sys->red, sizeof(hres), cudaMemcpyDeviceToHost, sys->s));
+  // orthonormalise and rebuild the exchange data / observables of Psi_{n+1}
+  PT_TRY(orthonormalize(sys, sys->psi_f, sys->psi));
+  PT_TRY(state_from_psi(sys));
+  if (fixed > 0) drho = hres[1] * sys->dV / (2.0 * ne);
+  if (info) {
+    info->scf_iters = it;
+    info->converged = converged ? 1 : 0;
+    info->resid_norm = std::sqrt(hres[0]);
+    info->drho = drho;
+    info->energy = sys->energy;
+    for (int k = 0; k < 3; ++k) info->dipole[k] = sys->dipole[k];
+  }
+  return converged ? PT_OK : PT_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+pt_status pt_basis_size(const pt_params* p, int* npw) {
+  std::string why;
+  pt_status st = check_params(p, &why);
+  if (st != PT_OK) { g_last_error = why; return st; }
+  if (npw == nullptr) { g_last_error = "npw is NULL"; return PT_ERR_INVALID; }
+  std::vector<int> idx;
+  basis_list(p, &idx, nullptr);
+  *npw = (int)idx.size();
+  return PT_OK;
+}
+
+pt_status pt_basis_indices(const pt_params* p, int64_t* out_host) {
+  std::string why;
+  pt_status st = check_params(p, &why);
+  if (st != PT_OK) { g_last_error = why; return st; }
+  if (out_host == nullptr) { g_last_error = "out is NULL"; return PT_ERR_INVALID; }
+  std::vector<int> idx;
+  basis_list(p, &idx, nullptr);
+  for (size_t k = 0; k < idx.size(); ++k) out_host[k] = idx[k];
+  return PT_OK;
+}
+
+pt_status pt_workspace_size(const pt_params* p, size_t* bytes) {
+  std::string why;
+  pt_status st = check_params(p, &why);
+  if (st != PT_OK) { g_last_error = why; return st; }
+  if (bytes == nullptr) { g_last_error = "bytes is NULL"; return PT_ERR_INVALID; }
+  *bytes = carve(nullptr, p, 0);
+  return PT_OK;
+}
+
+static pt_status init_body(pt_system* sys, const double* psi0_host) {
+  const pt_params* p = &sys->p;
+  std::vector<int> idx;
+  std::vector<double> g2;
+  basis_list(p, &idx, &g2);
+  const int npw = sys->npw;
+  // host tables
+  std::vector<double> kin(npw);
+  {
+    int k = 0;
+    for (int t : idx) {
+      const int i2 = t % p->n[2], i1 = (t / p->n[2]) % p->n[1], i0 = t / (p->n[1] * p->n[2]);
+      const double gk0 = 2.0 * M_PI * freq(i0, p->n[0]) / p->cell[0] + p->kick[0];
+      const double gk1 = 2.0 * M_PI * freq(i1, p->n[1]) / p->cell[1] + p->kick[1];
+      const double gk2 = 2.0 * M_PI * freq(i2, p->n[2]) / p->cell[2] + p->kick[2];
+      kin[k++] = 0.5 * (gk0 * gk0 + gk1 * gk1 + gk2 * gk2);
+    }
+  }
+  std::vector<double2> tw(pt::kTwiddleTotal);
+  pt::twiddle_host(tw.data());
+  std::vector<float2> tw32(pt::kTwiddleTotal);
+  for (int t = 0; t < pt::kTwiddleTotal; ++t) tw32[t] = make_float2((float)tw[t].x, (float)tw[t].y);
+  // screened kernel in the pair-intermediate layout [i2][i0][i1], scaled by -alpha / N
+  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+  const double w2 = p->omega * p->omega;
+  std::vector<double> kt((size_t)sys->N);
+  for (int i2 = 0; i2 < n2; ++i2)
+    for (int i0 = 0; i0 < n0; ++i0)
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const double g0 = 2.0 * M_PI * freq(i0, n0) / p->cell[0];
+        const double g1 = 2.0 * M_PI * freq(i1, n1) / p->cell[1];
+        const double gz = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
+        const double gg = g0 * g0 + g1 * g1 + gz * gz;
+        const double k = gg > 0.0 ? 4.0 * M_PI * (-std::expm1(-gg / (4.0 * w2))) / gg : M_PI / w2;
+        kt[((size_t)i2 * n0 + i0) * n1 + i1] = -p->alpha * k / (double)sys->N;
+      }
+  cudaStream_t s = sys->s;
+  PT_CK(cudaMemcpyAsync(sys->basis, idx.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(sys->kin, kin.data(), sizeof(double) * npw, cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(sys->tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(sys->tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice, s));
+  if (sys->mixed) {
+    std::vector<float> kf(kt.size());
+    for (size_t t = 0; t < kt.size(); ++t) kf[t] = (float)kt[t];
+    PT_CK(cudaMemcpyAsync(sys->khat32, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaStreamSynchronize(s));
+  } else {
+    PT_CK(cudaMemcpyAsync(sys->khat64, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice, s));
+  }
+  if (p->n_atoms > 0)
+    PT_CK(cudaMemcpyAsync(sys->d_atoms, sys->atoms.data(), sizeof(double) * 3 * p->n_atoms, cudaMemcpyHostToDevice, s));
+  sys->tw.d64 = sys->tw64;
+  sys->tw.d32 = sys->tw32;
+  // pair tiles of the symmetric exchange
+  {
+    pt::PairTile* tiles = nullptr;
+    int *lf = nullptr, *lc = nullptr, nl = 0;
+    const int tile = choose_tile(p);
+    const int tpl = tiles_per_launch(p, sys->N, sys->mixed);
+    const int nt = pt::fock_build_tiles(sys->ne, 0, tile, 1, tpl, &tiles, &lf, &lc, &nl);
+    if (nt < 0) { sys->err = "tile schedule"; return PT_ERR_INVALID; }
+    PT_CK(cudaMemcpyAsync(sys->d_tiles_sym, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, s));
+    PT_CK(cudaStreamSynchronize(s));
+    std::free(tiles);
+    sys->plan_sym.tile = tile;
+    sys->plan_sym.tiles_per_launch = tpl;
+    sys->plan_sym.n_launch = nl;
+    sys->plan_sym.launch_first = lf;
+    sys->plan_sym.launch_count = lc;
+    sys->plan_sym.d_tiles = sys->d_tiles_sym;
+    sys->plan_sym.n_tiles = nt;
+  }
+  PT_CK(cudaStreamSynchronize(s));
+  // device tables
+  PT_CK(pt::hartree_factor(sys->hfac, sys->g, p->cell, s));
+  if (p->n_atoms > 0)
+    PT_CK(pt::ion_potential(sys->vion, sys->g, p->cell, sys->d_atoms, p->n_atoms, p->well_depth, p->well_sigma, s));
+  else
+    PT_CK(cudaMemsetAsync(sys->vion, 0, sizeof(double) * sys->N, s));
+  // start orbitals
+  if (psi0_host == nullptr) { sys->err = "psi0_host is NULL"; return PT_ERR_INVALID; }
+  PT_CK(cudaMemcpyAsync(sys->tmp, psi0_host, sizeof(double2) * npw * sys->ne, cudaMemcpyHostToDevice, s));
+  PT_TRY(orthonormalize(sys, sys->tmp, sys->psi));
+  PT_TRY(relax(sys));
+  PT_TRY(state_from_psi(sys));
+  PT_CK(cudaStreamSynchronize(s));
+  PT_CK(cudaGetLastError());
+  return PT_OK;
+}
+
+pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_workspace, size_t workspace_bytes,
+                         void* stream, pt_system** out) {
+  std::string why;
+  pt_status st = check_params(p, &why);
+  if (st != PT_OK) { g_last_error = why; return st; }
+  if (out == nullptr || d_workspace == nullptr) { g_last_error = "out / workspace is NULL"; return PT_ERR_INVALID; }
+  if (((uintptr_t)d_workspace & 255) != 0) { g_last_error = "workspace must be 256-byte aligned"; return PT_ERR_INVALID; }
+  const size_t need = carve(nullptr, p, 0);
+  if (workspace_bytes < need) { g_last_error = "workspace too small"; return PT_ERR_OOM; }
+  pt_system* sys = new pt_system();
+  sys->p = *p;
+  if (p->n_atoms > 0) sys->atoms.assign(p->atom_frac, p->atom_frac + 3 * p->n_atoms);
+  sys->p.atom_frac = nullptr;
+  sys->s = (cudaStream_t)stream;
+  sys->g = Grid3{p->n[0], p->n[1], p->n[2]};
+  sys->N = sys->g.N();
+  std::vector<int> idx;
+  basis_list(p, &idx, nullptr);
+  sys->npw = (int)idx.size();
+  sys->ne = p->n_orb;
+  sys->mdim = p->anderson_dim;
+  sys->hb = h_batch(p);
+  sys->vol = p->cell[0] * p->cell[1] * p->cell[2];
+  sys->dV = sys->vol / (double)sys->N;
+  sys->mixed = p->precision == PT_MIXED;
+  carve(sys, p, (uintptr_t)d_workspace);
+  st = init_body(sys, psi0_host);
+  if (st != PT_OK) {
+    g_last_error = sys->err;
+    std::free(sys->plan_sym.launch_first);
+    std::free(sys->plan_sym.launch_count);
+    std::free(sys->plan_x.launch_first);
+    std::free(sys->plan_x.launch_count);
+    delete sys;
+    return st;
+  }
+  *out = sys;
+  return PT_OK;
+}
+
+pt_status pt_build_ace(pt_system* sys) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
+  sys->psi_r_current = true;
+  const int saved = sys->p.fock_mode;
+  sys->p.fock_mode = PT_FOCK_ACE;
+  pt_status st = exchange_data(sys);
+  sys->p.fock_mode = saved;
+  if (st != PT_OK) return st;
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+pt_status pt_apply_h(pt_system* sys, const void* d_X, void* d_Y, int ncols, int fock_mode) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  if (d_X == nullptr || d_Y == nullptr || ncols < 1 || ncols > sys->ne) {
+    sys->err = "pt_apply_h: need 1 <= ncols <= n_orb and non-NULL buffers";
+    return PT_ERR_INVALID;
+  }
+  if (fock_mode == PT_FOCK_ACE && !sys->have_ace) { sys->err = "pt_apply_h: no ACE operator built"; return PT_ERR_INVALID; }
+  const double2* X = (const double2*)d_X;
+  double2* Y = (double2*)d_Y;
+  if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
+  sys->psi_r_current = true;
+  PT_CK(pt::density(sys->psi_r, sys->N, sys->ne, sys->rho, sys->s));
+  PT_TRY(local_potential(sys));
+  PT_TRY(apply_local(sys, X, Y, ncols));
+  if (sys->p.alpha != 0.0) {
+    if (fock_mode == PT_FOCK_EXACT) {
+      if (sys->mixed) PT_TRY(exchange_x_t<float>(sys, X, ncols, Y));
+      else PT_TRY(exchange_x_t<double>(sys, X, ncols, Y));
+    } else if (fock_mode == PT_FOCK_ACE) {
+      PT_TRY(ace_apply(sys, X, ncols, Y));
+    }
+  }
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+pt_status pt_exchange(pt_system* sys, void* d_W) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  if (d_W == nullptr) { sys->err = "pt_exchange: NULL output"; return PT_ERR_INVALID; }
+  if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
+  sys->psi_r_current = true;
+  PT_TRY(exchange_sym(sys, (double2*)d_W, 0));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+pt_status pt_cn_step(pt_system* sys, pt_step_info* out) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  pt_step_info info{};
+  pt_status st = cn_step(sys, &info);
+  if (out) *out = info;
+  return st;
+}
+
+pt_status pt_propagate(pt_system* sys, int nsteps, pt_step_info* out_host) {
+  if (sys == nullptr || nsteps < 0) return PT_ERR_INVALID;
+  pt_status worst = PT_OK;
+  for (int k = 0; k < nsteps; ++k) {
+    pt_step_info info{};
+    pt_status st = cn_step(sys, &info);
+    if (out_host) out_host[k] = info;
+    if (st == PT_ERR_NOT_CONVERGED) { worst = st; continue; }
+    if (st != PT_OK) return st;
+  }
+  return worst;
+}
+
+pt_status pt_get_orbitals(pt_system* sys, double* psi_host) {
+  if (sys == nullptr || psi_host == nullptr) return PT_ERR_INVALID;
+  PT_CK(cudaMemcpyAsync(psi_host, sys->psi, sizeof(double2) * sys->npw * sys->ne, cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+pt_status pt_set_orbitals(pt_system* sys, const double* psi_host) {
+  if (sys == nullptr || psi_host == nullptr) return PT_ERR_INVALID;
+  PT_CK(cudaMemcpyAsync(sys->tmp, psi_host, sizeof(double2) * sys->npw * sys->ne, cudaMemcpyHostToDevice, sys->s));
+  PT_TRY(orthonormalize(sys, sys->tmp, sys->psi));
+  PT_TRY(state_from_psi(sys));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+pt_status pt_observables(pt_system* sys, double* energy, double* dipole) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  if (energy) *energy = sys->energy;
+  if (dipole) for (int k = 0; k < 3; ++k) dipole[k] = sys->dipole[k];
+  return PT_OK;
+}
+
+pt_status pt_orbitals_device(pt_system* sys, void** d_psi) {
+  if (sys == nullptr || d_psi == nullptr) return PT_ERR_INVALID;
+  *d_psi = sys->psi;
+  return PT_OK;
+}
+
+pt_status pt_destroy(pt_system* sys) {
+  if (sys == nullptr) return PT_OK;
+  std::free(sys->plan_sym.launch_first);
+  std::free(sys->plan_sym.launch_count);
+  std::free(sys->plan_x.launch_first);
+  std::free(sys->plan_x.launch_count);
+  delete sys;
+  return PT_OK;
+}
+
+const char* pt_last_error(const pt_system* sys) {
+  if (sys == nullptr) return g_last_error.c_str();
+  return sys->err.empty() ? "no error" : sys->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+namespace pt {
+
+// Supported FFT lengths and the offset of each length's twiddle table.
+constexpr int kNumLengths = 8;
+constexpr int kLengths[kNumLengths] = {8, 12, 16, 24, 32, 48, 64, 96};
+constexpr int kTwiddleTotal = 8 + 12 + 16 + 24 + 32 + 48 + 64 + 96;
+int twiddle_offset(int L);   // -1 if unsupported
+void twiddle_host(double2* out);   // all tables, exp(-2 pi i t / L)
+
+struct Grid3 {
+  int n0, n1, n2;
+  long N() const { return (long)n0 * n1 * n2; }
+};
+
+// Twiddle tables resident on the device (per precision).
+struct DevTwiddles {
+  const double2* d64;
+  const float2* d32;
+  template <typename T> const void* base() const;
+};
+
+// ---- generic batched 3D transforms (fft3d.cu) -----------------------------
+// Volumes are [v][i0][i1][i2] (axis 2 fastest), `nvol` of them, in place.
+// dir: +1 inverse (exp(+i...)), -1 forward. Scale applied at the end of the pass.
+template <typename T>
+cudaError_t fft_rows(const void* in, void* out, long nvol, Grid3 g, int inverse, double scale,
+                     const T* mul_real, const DevTwiddles& tw, cudaStream_t s);
+// axis in {0, 1}. mode 0: one transform; mode 1 (axis 0 only): inverse, multiply
+// by mul_real (natural layout), forward; mode 2 (axis 0 only): forward,
+// multiply by mul_real, inverse.
+template <typename T>
+cudaError_t fft_cols(void* data, long nvol, Grid3 g, int axis, int inverse, int mode, double scale,
+                     const T* mul_real, const DevTwiddles& tw, cudaStream_t s);
+// out[v][basis[k]] = scale * in[v][k] (in: complex128 coefficients), zero elsewhere.
+template <typename T>
+cudaError_t scatter_basis(const double2* in, long in_ld, void* out, long nvol, Grid3 g, const int* basis,
+                          int npw, double scale, cudaStream_t s);
+// out[v][k] = kin_scale * kin[k] * x[v][k] + scale * in[v][basis[k]] (+ out if accumulate)
+template <typename T>
+cudaError_t gather_basis(const void* in, double2* out, long out_ld, long nvol, Grid3 g, const int* basis,
+                         int npw, double scale, const double* kin, const double2* x, long x_ld, int accumulate,
+                         cudaStream_t s);
+cudaError_t convert_c128_to_c64(const double2* in, float2* out, long n, cudaStream_t s);
+
+// ---- Fock exchange pair pipeline (fock.cu) ----------------------------------
+constexpr int kTileMax = 4;
+struct PairTile {
+  int n_orb;
+  int n_pairs;
+  int orb[2 * kTileMax];
+  signed char src[2 * kTileMax];     // 0: occupied orbitals, 1: X columns
+  signed char is_out[2 * kTileMax];  // accumulate into this orbital's W
+  signed char pi[kTileMax * kTileMax];
+  signed char pj[kTileMax * kTileMax];
+};
+
+struct FockPlan {
+  int tile;               // orbitals per tile edge
+  int tiles_per_launch;   // cap on tiles in one pass triple
+  // launches: [first_tile, count) ranges into the device tile array
+  int n_launch;
+  int* launch_first;      // host arrays
+  int* launch_count;
+  PairTile* d_tiles;      // device
+  int n_tiles;
+};
+
+template <typename T>
+cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
+                       Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s);
+size_t fock_scratch_elems(const FockPlan& plan, Grid3 g);
+// Host tile schedules. sym: pairs i <= j of n_occ orbitals; otherwise n_occ x n_x pairs.
+int fock_build_tiles(int n_occ, int n_x, int tile, int sym, int tiles_per_launch, PairTile** tiles_out,
+                     int** launch_first, int** launch_count, int* n_launch);
+
+// ---- dense linear algebra (linalg.cu) -------------------------------------
+// C(M x N) = alpha * op(A) op(B) + beta * C, complex, column-major, batched by strides.
+// A element (i, k) of op(A) == N: A[i + k * lda]; == H: conj(A[k + i * lda]).
+// Inputs stored as complex128; Tc is the compute / accumulate precision.
+enum { OP_N = 0, OP_H = 1 };
+template <typename Tc>
+cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const double2* A, long lda, long strideA,
+                 const double2* B, long ldb, long strideB, double2 beta, double2* C, long ldc, long strideC,
+                 int batch, double2* splitk_ws, size_t splitk_ws_elems, cudaStream_t s);
+// In-place lower Cholesky of an n x n Hermitian matrix (column-major, lower
+// triangle used and overwritten, upper set to 0). *d_status = 1 on a
+// non-positive pivot.
+cudaError_t cholesky(double2* A, int n, int* d_status, cudaStream_t s);
+// Linv = L^{-1} for lower-triangular L (n x n, column-major).
+cudaError_t tri_inverse(const double2* L, double2* Linv, int n, cudaStream_t s);
+
+// ---- elementwise / reductions (ptcn.cu) -------------------------------------
+// Deterministic sums: partial sums per block then a single-block final pass.
+cudaError_t reduce_norm2(const double2* x, long n, double* partials, int npart, double* out, cudaStream_t s);
+
+std::string cuda_msg(cudaError_t e);
+
+}  // namespace pt

@@ -1,0 +1,493 @@
+// Elementwise and reduction kernels of the PT-CN step (Alg. 1, Alg. 3,
+// Sec. 3.4) and of the local part of the Hamiltonian (Eq. 2).
+// Reductions are two-level (block partials, then one block sums the
+// partials in order), so every sum is deterministic.
+#include <cmath>
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "kernels.h"
+
+namespace pt {
+
+static inline unsigned nblk(long n, int thr, long cap = 152L * 16) {
+  return (unsigned)std::max<long>(1, std::min<long>((n + thr - 1) / thr, cap));
+}
+
+// ---- block reduction helper (fixed order) ----------------------------------
+template <int NS>
+__device__ __forceinline__ void block_sums(double (&v)[NS], double* part) {
+  __shared__ double sh[NS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double x = v[s];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[s][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    const int nw = blockDim.x >> 5;
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[threadIdx.x][w];
+    part[blockIdx.x * NS + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_finalize(const double* __restrict__ part, int nblocks, int ns, double* __restrict__ out) {
+  const int s = threadIdx.x;
+  if (s >= ns) return;
+  double t = 0.0;
+  for (int b = 0; b < nblocks; ++b) t += part[b * ns + s];
+  out[s] = t;
+}
+
+// ---- density ------------------------------------------------------------------
+__global__ void k_density(const double2* __restrict__ psi_r, long N, int ne, double* __restrict__ rho) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < N; r += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < ne; ++k) {
+      const double2 v = psi_r[(long)k * N + r];
+      s += v.x * v.x + v.y * v.y;
+    }
+    rho[r] = 2.0 * s;
+  }
+}
+
+cudaError_t density(const double2* psi_r, long N, int ne, double* rho, cudaStream_t s) {
+  k_density<<<nblk(N, 256, 152L * 64), 256, 0, s>>>(psi_r, N, ne, rho);
+  return cudaGetLastError();
+}
+
+// ---- local potential -----------------------------------------------------------
+__global__ void k_rho_to_complex(const double* __restrict__ rho, double2* __restrict__ buf, long N) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < N; r += (long)gridDim.x * blockDim.x)
+    buf[r] = make_double2(rho[r], 0.0);
+}
+
+__global__ void k_vloc(const double* __restrict__ vion, const double2* __restrict__ vh_c, const double* __restrict__ rho,
+                       long N, int use_h, double w_lda, double* __restrict__ vh, double* __restrict__ vloc) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < N; r += (long)gridDim.x * blockDim.x) {
+    double v = vion[r];
+    if (use_h) {
+      const double h = vh_c[r].x;
+      vh[r] = h;
+      v += h;
+    }
+    if (w_lda != 0.0) v += w_lda * (-cbrt(3.0 * rho[r] / M_PI));
+    vloc[r] = v;
+  }
+}
+
+cudaError_t rho_to_complex(const double* rho, double2* buf, long N, cudaStream_t s) {
+  k_rho_to_complex<<<nblk(N, 256), 256, 0, s>>>(rho, buf, N);
+  return cudaGetLastError();
+}
+
+cudaError_t assemble_vloc(const double* vion, const double2* vh_c, const double* rho, long N, int use_h, double w_lda,
+                          double* vh, double* vloc, cudaStream_t s) {
+  k_vloc<<<nblk(N, 256), 256, 0, s>>>(vion, vh_c, rho, N, use_h, w_lda, vh, vloc);
+  return cudaGetLastError();
+}
+
+// Gaussian wells summed over atoms and periodic images in real space.
+__global__ void k_vion(double* __restrict__ v, int n0, int n1, int n2, double a0, double a1, double a2,
+                       const double* __restrict__ atoms, int na, double depth, double sigma, double rcut) {
+  const long N = (long)n0 * n1 * n2;
+  const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+  const int m0 = (int)ceil(rcut / a0), m1 = (int)ceil(rcut / a1), m2 = (int)ceil(rcut / a2);
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x) {
+    const int i2 = (int)(t % n2);
+    const int i1 = (int)((t / n2) % n1);
+    const int i0 = (int)(t / ((long)n1 * n2));
+    const double x = a0 * i0 / n0, y = a1 * i1 / n1, z = a2 * i2 / n2;
+    double s = 0.0;
+    for (int a = 0; a < na; ++a) {
+      const double ax = atoms[3 * a] * a0, ay = atoms[3 * a + 1] * a1, az = atoms[3 * a + 2] * a2;
+      for (int p = -m0; p <= m0; ++p) {
+        const double dx = x - ax - p * a0;
+        if (fabs(dx) > rcut) continue;
+        for (int q = -m1; q <= m1; ++q) {
+          const double dy = y - ay - q * a1;
+          if (fabs(dy) > rcut) continue;
+          for (int w = -m2; w <= m2; ++w) {
+            const double dz = z - az - w * a2;
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 <= rcut * rcut) s += exp(-d2 * inv2s2);
+          }
+        }
+      }
+    }
+    v[t] = -depth * s;
+  }
+}
+
+cudaError_t ion_potential(double* v, Grid3 g, const double* cell, const double* d_atoms, int na, double depth,
+                          double sigma, cudaStream_t s) {
+  // exp(-d^2 / (2 sigma^2)) < 1e-20 beyond rcut
+  const double rcut = sigma * std::sqrt(2.0 * 46.0);
+  k_vion<<<nblk(g.N(), 128, 152L * 64), 128, 0, s>>>(v, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2], d_atoms, na,
+                                                     depth, sigma, rcut);
+  return cudaGetLastError();
+}
+
+// ---- PT residual (Alg. 1 and Alg. 3) ---------------------------------------------
+// psi_half = psi - i dt/2 R
+__global__ void k_half_step(const double2* __restrict__ psi, const double2* __restrict__ R, double hdt,
+                            double2* __restrict__ out, long n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double2 p = psi[t], r = R[t];
+    // -i hdt (rx + i ry) = hdt ry - i hdt rx
+    out[t] = make_double2(p.x + hdt * r.y, p.y - hdt * r.x);
+  }
+}
+
+cudaError_t half_step(const double2* psi, const double2* R, double hdt, double2* out, long n, cudaStream_t s) {
+  k_half_step<<<nblk(n, 256), 256, 0, s>>>(psi, R, hdt, out, n);
+  return cudaGetLastError();
+}
+
+// r = -(psi_f + i dt/2 T - psi_half); block partials of |r|^2
+__global__ void k_resid(const double2* __restrict__ psi_f, const double2* __restrict__ T, const double2* __restrict__ ph,
+                        double hdt, double2* __restrict__ r, long n, double* __restrict__ part) {
+  double acc[1] = {0.0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double2 p = psi_f[t], q = T[t], h = ph[t];
+    // i hdt (qx + i qy) = -hdt qy + i hdt qx
+    const double2 R = make_double2(p.x - hdt * q.y - h.x, p.y + hdt * q.x - h.y);
+    r[t] = make_double2(-R.x, -R.y);
+    acc[0] += R.x * R.x + R.y * R.y;
+  }
+  block_sums<1>(acc, part);
+}
+
+cudaError_t pt_residual(const double2* psi_f, const double2* T, const double2* ph, double hdt, double2* r, long n,
+                        double* part, double* out_norm2, cudaStream_t s) {
+  const unsigned b = nblk(n, 256, 1024);
+  k_resid<<<b, 256, 0, s>>>(psi_f, T, ph, hdt, r, n, part);
+  k_finalize<<<1, 32, 0, s>>>(part, b, 1, out_norm2);
+  return cudaGetLastError();
+}
+
+// y = x - tau * P * R, P = 1 / (1 + kin) per basis vector (start-state relaxation)
+__global__ void k_precond_step(double2* __restrict__ x, const double2* __restrict__ R, const double* __restrict__ kin,
+                               int npw, long n, double tau) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double p = tau / (1.0 + kin[t % npw]);
+    const double2 r = R[t];
+    double2 v = x[t];
+    v.x -= p * r.x;
+    v.y -= p * r.y;
+    x[t] = v;
+  }
+}
+
+cudaError_t precond_step(double2* x, const double2* R, const double* kin, int npw, long n, double tau, cudaStream_t s) {
+  k_precond_step<<<nblk(n, 256), 256, 0, s>>>(x, R, kin, npw, n, tau);
+  return cudaGetLastError();
+}
+
+// ---- Anderson mixing (Sec. 3.4), per band -------------------------------------------
+// push: dX[slot] = x - x_prev, dR[slot] = r - r_prev (when have_prev), then x_prev = x, r_prev = r
+__global__ void k_anderson_push(const double2* __restrict__ x, const double2* __restrict__ r, double2* __restrict__ xp,
+                                double2* __restrict__ rp, double2* __restrict__ dx, double2* __restrict__ dr, long n,
+                                int have_prev) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double2 a = x[t], b = r[t];
+    if (have_prev) {
+      const double2 c = xp[t], d = rp[t];
+      dx[t] = make_double2(a.x - c.x, a.y - c.y);
+      dr[t] = make_double2(b.x - d.x, b.y - d.y);
+    }
+    xp[t] = a;
+    rp[t] = b;
+  }
+}
+
+cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, double2* dx, double2* dr,
+                          long n, int have_prev, cudaStream_t s) {
+  k_anderson_push<<<nblk(n, 256), 256, 0, s>>>(x, r, xp, rp, dx, dr, n, have_prev);
+  return cudaGetLastError();
+}
+
+// For each band b: gram[b][slot_q][new] = <dR_{slot_q}, dR_new>_b (and its
+// conjugate at [new][slot_q]) and rhs[b][q] = <dR_{slot_q}, r>_b for the
+// history slots in order (oldest first). One block per band; the slots are
+// processed four at a time to bound registers.
+__global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride, SlotList sl, int newslot,
+                                const double2* __restrict__ r, int npw, int mdim, double2* __restrict__ gram,
+                                double2* __restrict__ rhs) {
+  const int b = blockIdx.x;
+  const int k = sl.k;
+  const long boff = (long)b * npw;
+  const double2* dn = dR + (long)newslot * slot_stride + boff;
+  const double2* rb = r + boff;
+  __shared__ double sh[16][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q0 = 0; q0 < k; q0 += 4) {
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+      const double2 vn = dn[g], vr = rb[g];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        if (q0 + qq < k) {
+          const double2 u = dR[(long)sl.s[q0 + qq] * slot_stride + boff + g];
+          acc[4 * qq + 0] += u.x * vn.x + u.y * vn.y;
+          acc[4 * qq + 1] += u.x * vn.y - u.y * vn.x;
+          acc[4 * qq + 2] += u.x * vr.x + u.y * vr.y;
+          acc[4 * qq + 3] += u.x * vr.y - u.y * vr.x;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      double x = acc[c];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) sh[c][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && q0 + (int)threadIdx.x < k) {
+      const int qq = threadIdx.x, q = q0 + qq;
+      double v[4];
+      for (int c = 0; c < 4; ++c) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh[4 * qq + c][w];
+        v[c] = t;
+      }
+      const long gb = (long)b * mdim * mdim;
+      const int sq = sl.s[q];
+      if (sq == newslot) {
+        gram[gb + (long)sq * mdim + sq] = make_double2(v[0], 0.0);
+      } else {
+        gram[gb + (long)sq * mdim + newslot] = make_double2(v[0], v[1]);
+        gram[gb + (long)newslot * mdim + sq] = make_double2(v[0], -v[1]);
+      }
+      rhs[(long)b * mdim + q] = make_double2(v[2], v[3]);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t anderson_dots(const double2* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
+                          int npw, int ne, int mdim, double2* gram, double2* rhs, cudaStream_t s) {
+  if (sl.k > kSlotMax) return cudaErrorInvalidValue;
+  k_anderson_dots<<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
+  return cudaGetLastError();
+}
+
+// Solve (G + 1e-14 tr(G) I) gamma = rhs per band by Cholesky; gamma = 0 when
+// the trace is zero or a pivot is not positive. One thread per band.
+__global__ void k_anderson_solve(const double2* __restrict__ gram, const double2* __restrict__ rhs, SlotList sl,
+                                 int mdim, int ne, double2* __restrict__ gamma) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ne) return;
+  const int k = sl.k;
+  double2 L[kSlotMax][kSlotMax];
+  double2 y[kSlotMax];
+  const long gb = (long)b * mdim * mdim;
+  double tr = 0.0;
+  for (int q = 0; q < k; ++q) tr += gram[gb + (long)sl.s[q] * mdim + sl.s[q]].x;
+  bool ok = tr > 0.0;
+  const double shift = 1e-14 * tr;
+  // L L^H = A with A[i][j] = G[s_i][s_j]  (G[s][t] = <dR_s, dR_t>)
+  for (int j = 0; j < k && ok; ++j) {
+    double d = gram[gb + (long)sl.s[j] * mdim + sl.s[j]].x + shift;
+    for (int p = 0; p < j; ++p) d -= L[j][p].x * L[j][p].x + L[j][p].y * L[j][p].y;
+    if (!(d > 0.0)) { ok = false; break; }
+    const double ljj = sqrt(d);
+    L[j][j] = make_double2(ljj, 0.0);
+    for (int i = j + 1; i < k; ++i) {
+      double2 a = gram[gb + (long)sl.s[i] * mdim + sl.s[j]];
+      for (int p = 0; p < j; ++p) {
+        // a -= L[i][p] * conj(L[j][p])
+        a.x -= L[i][p].x * L[j][p].x + L[i][p].y * L[j][p].y;
+        a.y -= L[i][p].y * L[j][p].x - L[i][p].x * L[j][p].y;
+      }
+      L[i][j] = make_double2(a.x / ljj, a.y / ljj);
+    }
+  }
+  if (!ok) {
+    for (int q = 0; q < k; ++q) gamma[(long)b * mdim + q] = make_double2(0.0, 0.0);
+    return;
+  }
+  for (int i = 0; i < k; ++i) {   // L y = rhs
+    double2 a = rhs[(long)b * mdim + i];
+    for (int p = 0; p < i; ++p) {
+      a.x -= L[i][p].x * y[p].x - L[i][p].y * y[p].y;
+      a.y -= L[i][p].x * y[p].y + L[i][p].y * y[p].x;
+    }
+    y[i] = make_double2(a.x / L[i][i].x, a.y / L[i][i].x);
+  }
+  for (int i = k - 1; i >= 0; --i) {   // L^H g = y
+    double2 a = y[i];
+    for (int p = i + 1; p < k; ++p) {
+      const double2 gp = y[p];
+      a.x -= L[p][i].x * gp.x + L[p][i].y * gp.y;
+      a.y -= L[p][i].x * gp.y - L[p][i].y * gp.x;
+    }
+    y[i] = make_double2(a.x / L[i][i].x, a.y / L[i][i].x);
+  }
+  for (int q = 0; q < k; ++q) gamma[(long)b * mdim + q] = y[q];
+}
+
+cudaError_t anderson_solve(const double2* gram, const double2* rhs, const SlotList& sl, int mdim, int ne,
+                           double2* gamma, cudaStream_t s) {
+  k_anderson_solve<<<(ne + 63) / 64, 64, 0, s>>>(gram, rhs, sl, mdim, ne, gamma);
+  return cudaGetLastError();
+}
+
+// x <- x + beta r - sum_q (dX_q + beta dR_q) gamma_q  (per band)
+__global__ void k_anderson_update(double2* __restrict__ x, const double2* __restrict__ r,
+                                  const double2* __restrict__ dX, const double2* __restrict__ dR, long slot_stride,
+                                  SlotList sl, const double2* __restrict__ gamma, int mdim, int npw, long n,
+                                  double beta) {
+  const int k = sl.k;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / npw;
+    double2 v = x[t];
+    const double2 rr = r[t];
+    v.x += beta * rr.x;
+    v.y += beta * rr.y;
+    for (int q = 0; q < k; ++q) {
+      const double2 g = gamma[b * mdim + q];
+      const double2 a = dX[(long)sl.s[q] * slot_stride + t];
+      const double2 c = dR[(long)sl.s[q] * slot_stride + t];
+      const double2 u = make_double2(a.x + beta * c.x, a.y + beta * c.y);
+      v.x -= u.x * g.x - u.y * g.y;
+      v.y -= u.x * g.y + u.y * g.x;
+    }
+    x[t] = v;
+  }
+}
+
+cudaError_t anderson_update(double2* x, const double2* r, const double2* dX, const double2* dR, long slot_stride,
+                            const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta,
+                            cudaStream_t s) {
+  k_anderson_update<<<nblk(n, 256), 256, 0, s>>>(x, r, dX, dR, slot_stride, sl, gamma, mdim, npw, n, beta);
+  return cudaGetLastError();
+}
+
+// ---- density change, energy, dipole ---------------------------------------------------
+__global__ void k_drho(const double* __restrict__ a, const double* __restrict__ b, long N, double* __restrict__ part) {
+  double acc[1] = {0.0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x)
+    acc[0] += fabs(a[t] - b[t]);
+  block_sums<1>(acc, part);
+}
+
+cudaError_t rho_change(const double* a, const double* b, long N, double* part, double* out, cudaStream_t s) {
+  const unsigned nb = nblk(N, 256, 1024);
+  k_drho<<<nb, 256, 0, s>>>(a, b, N, part);
+  k_finalize<<<1, 32, 0, s>>>(part, nb, 1, out);
+  return cudaGetLastError();
+}
+
+// grid sums: [0] vion*rho, [1] vh*rho, [2] rho^{4/3}, [3..5] r*rho
+__global__ void k_grid_sums(const double* __restrict__ rho, const double* __restrict__ vion,
+                            const double* __restrict__ vh, int use_h, int n0, int n1, int n2, double a0, double a1,
+                            double a2, double* __restrict__ part) {
+  const long N = (long)n0 * n1 * n2;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x) {
+    const int i2 = (int)(t % n2);
+    const int i1 = (int)((t / n2) % n1);
+    const int i0 = (int)(t / ((long)n1 * n2));
+    const double p = rho[t];
+    acc[0] += vion[t] * p;
+    if (use_h) acc[1] += vh[t] * p;
+    acc[2] += cbrt(p) * p;
+    acc[3] += (a0 * i0 / n0) * p;
+    acc[4] += (a1 * i1 / n1) * p;
+    acc[5] += (a2 * i2 / n2) * p;
+  }
+  block_sums<6>(acc, part);
+}
+
+// [0] sum kin |c|^2
+__global__ void k_kin_sum(const double2* __restrict__ c, const double* __restrict__ kin, int npw, long n,
+                          double* __restrict__ part) {
+  double acc[1] = {0.0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double2 v = c[t];
+    acc[0] += kin[t % npw] * (v.x * v.x + v.y * v.y);
+  }
+  block_sums<1>(acc, part);
+}
+
+__global__ void k_trace_real(const double2* __restrict__ M, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += M[i + (long)i * n].x;
+    *out = t;
+  }
+}
+
+cudaError_t energy_sums(const double* rho, const double* vion, const double* vh, int use_h, Grid3 g, const double* cell,
+                        const double2* c, const double* kin, int npw, int ne, const double2* negM, double* part,
+                        double* out8, cudaStream_t s) {
+  const unsigned nb = nblk(g.N(), 256, 1024);
+  k_grid_sums<<<nb, 256, 0, s>>>(rho, vion, vh, use_h, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2], part);
+  k_finalize<<<1, 32, 0, s>>>(part, nb, 6, out8);
+  const long n = (long)npw * ne;
+  const unsigned nb2 = nblk(n, 256, 1024);
+  k_kin_sum<<<nb2, 256, 0, s>>>(c, kin, npw, n, part + 6 * 1024);
+  k_finalize<<<1, 32, 0, s>>>(part + 6 * 1024, nb2, 1, out8 + 6);
+  if (negM != nullptr) k_trace_real<<<1, 32, 0, s>>>(negM, ne, out8 + 7);
+  return cudaGetLastError();
+}
+
+__global__ void k_hartree_factor(double* __restrict__ f, int n0, int n1, int n2, double a0, double a1, double a2) {
+  const long N = (long)n0 * n1 * n2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x) {
+    const int i2 = (int)(t % n2);
+    const int i1 = (int)((t / n2) % n1);
+    const int i0 = (int)(t / ((long)n1 * n2));
+    const int m0 = i0 < (n0 + 1) / 2 ? i0 : i0 - n0;
+    const int m1 = i1 < (n1 + 1) / 2 ? i1 : i1 - n1;
+    const int m2 = i2 < (n2 + 1) / 2 ? i2 : i2 - n2;
+    const double g0 = 2.0 * M_PI * m0 / a0, g1 = 2.0 * M_PI * m1 / a1, g2 = 2.0 * M_PI * m2 / a2;
+    const double gg = g0 * g0 + g1 * g1 + g2 * g2;
+    f[t] = gg > 0.0 ? 4.0 * M_PI / (gg * (double)N) : 0.0;
+  }
+}
+
+cudaError_t hartree_factor(double* f, Grid3 g, const double* cell, cudaStream_t s) {
+  k_hartree_factor<<<nblk(g.N(), 256), 256, 0, s>>>(f, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2]);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_scaled(const double2* __restrict__ a, double2* __restrict__ b, long n, double s) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double2 v = a[t];
+    b[t] = make_double2(s * v.x, s * v.y);
+  }
+}
+
+cudaError_t copy_scaled(const double2* a, double2* b, long n, double sc, cudaStream_t s) {
+  k_copy_scaled<<<nblk(n, 256), 256, 0, s>>>(a, b, n, sc);
+  return cudaGetLastError();
+}
+
+}  // namespace pt
+
+namespace pt {
+
+__global__ void k_axpy(double2 a, const double2* __restrict__ x, double2* __restrict__ y, long n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double2 v = x[t];
+    double2 w = y[t];
+    w.x += a.x * v.x - a.y * v.y;
+    w.y += a.x * v.y + a.y * v.x;
+    y[t] = w;
+  }
+}
+
+cudaError_t axpy(double2 a, const double2* x, double2* y, long n, cudaStream_t s) {
+  k_axpy<<<nblk(n, 256), 256, 0, s>>>(a, x, y, n);
+  return cudaGetLastError();
+}
+
+}  // namespace pt

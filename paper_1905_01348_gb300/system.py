@@ -1,0 +1,80 @@
+"""A PT-CN system whose workspace and stream come from PyTorch (device memory plumbing only)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native as nat
+
+
+class System:
+    """Owns one pt_system handle and the device workspace it runs in.
+
+    params: workload dictionary (see synthetic.si_workload); psi0: (n_orb, npw)
+    complex128 start coefficients. The workspace is a torch uint8 tensor on
+    ``device``; all work is enqueued on torch's current stream of that device.
+    """
+
+    def __init__(self, params: dict, psi0: np.ndarray, device: str = "cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.params = nat.make_params(params)
+        self.npw = nat.pt_basis_size(self.params)
+        self.n_orb = self.params.n_orb
+        self.ws_bytes = nat.pt_workspace_size(self.params)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.handle = nat.pt_init_system(self.params, psi0, self.workspace.data_ptr(), self.ws_bytes,
+                                         self.stream.cuda_stream)
+
+    # -- state -------------------------------------------------------------
+    def orbitals(self) -> np.ndarray:
+        return nat.pt_get_orbitals(self.handle, self.n_orb, self.npw)
+
+    def set_orbitals(self, psi: np.ndarray) -> None:
+        nat.pt_set_orbitals(self.handle, psi)
+
+    def observables(self):
+        return nat.pt_observables(self.handle)
+
+    def orbitals_device(self):
+        """A torch view (n_orb, npw) complex128 of the current device orbitals."""
+        ptr = nat.pt_orbitals_device(self.handle)
+        base = self.workspace.data_ptr()
+        off = ptr - base
+        nbytes = self.n_orb * self.npw * 16
+        return self.workspace[off:off + nbytes].view(self.torch.complex128).view(self.n_orb, self.npw)
+
+    # -- operations ------------------------------------------------------------
+    def exchange(self):
+        """V_X Psi of the current orbitals as a (n_orb, npw) complex128 device tensor."""
+        out = self.torch.empty((self.n_orb, self.npw), dtype=self.torch.complex128, device=self.device)
+        nat.pt_exchange(self.handle, out.data_ptr())
+        return out
+
+    def apply_h(self, X, fock_mode: int = nat.PT_FOCK_EXACT):
+        """H X for a (m, npw) complex128 device tensor X (m <= n_orb)."""
+        X = X.contiguous()
+        Y = self.torch.empty_like(X)
+        nat.pt_apply_h(self.handle, X.data_ptr(), Y.data_ptr(), X.shape[0], fock_mode)
+        return Y
+
+    def build_ace(self) -> None:
+        nat.pt_build_ace(self.handle)
+
+    def step(self):
+        return nat.pt_cn_step(self.handle)
+
+    def propagate(self, nsteps: int):
+        return nat.pt_propagate(self.handle, nsteps)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None:
+            nat.pt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
