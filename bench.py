@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark: Fock pair-FFT solves/s (and wall-s per fs) of PT-CN steps on the
+Si216 workload (3x3x3 diamond supercell, a = 30.78 bohr, 432 doubly occupied
+orbitals, 96^3 grid, 10 Ha cutoff, Gaussian wells, HSE-like screened exchange
+w = 0.106 / bohr with mixing 0.25, ACE rebuilt once per step, dt = 50 as).
+
+A step is one PT-CN step (Eq. 5, Alg. 1) through the C ABI: the exchange of
+the new orbitals over all 93,528 unordered orbital pairs (pair product, 3D
+FFT, screened-kernel multiply, inverse FFT, accumulate), the ACE build
+(M = Psi^H W, Cholesky of -M, xi = W L^{-H}), and the SCF loop (local H,
+ACE apply, PT residual, per-band Anderson mixing, density) to the 1e-6
+density tolerance, then Cholesky orthonormalisation. value = unordered pair
+solves per second over the timed steps (all ranks), inputs resident in HBM.
+
+Multi-GPU: the path runs replicas only (independent trajectories per rank,
+no data-path collective); value sums the ranks' pairs over the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Fock pair-FFT solves/s (Si216 PT-CN steps, mixed precision)"
+UNIT = "pair-solves/s"
+STEPS_PER_FS = 20   # 50 as per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="si216", choices=["si8", "si64", "si216"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def pairs_per_exchange(n_orb: int) -> int:
+    return n_orb * (n_orb + 1) // 2
+
+
+def measured_peaks() -> dict:
+    """HBM GB/s and bf16 TFLOP/s measured on this machine, else the stated fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def pair_pipeline_bytes(n, mixed: bool, tile: int = 4) -> float:
+    """Algorithmic HBM bytes per unordered pair of the pair pipeline.
+
+    Four passes over the pair intermediate (F1 write, F2 read + write, F3
+    read) of N complex values, plus orbital reads and W accumulation amortised
+    over a tile of `tile` x `tile` pairs: (4 + 4 / tile) * N * sizeof(complex).
+    """
+    N = int(n[0]) * int(n[1]) * int(n[2])
+    cs = 8 if mixed else 16
+    return (4.0 + 4.0 / tile) * N * cs
+
+
+def traffic_per_launch(workload: str, precision: str):
+    """DRAM bytes per launch group from the committed ncu summary, if one matches."""
+    path = os.path.join(ROOT, "profiles", "fock_pair_pipeline_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get(f"{workload}-{precision}")
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_pairs_per_s(workload: str, budget_s: float = 15.0, seed: int = 0) -> dict:
+    """The FP64 oracle's pair loop timed on the host cores on a bounded sample.
+
+    Sample: m target orbitals against M occupied orbitals of the workload's
+    grid (random coefficients), i.e. M * m pair solves of the oracle's
+    apply_vx_real (each: product, dense FFT, kernel multiply, inverse FFT,
+    accumulate), repeated until the time budget is used.
+    """
+    import numpy as np
+    import synthetic as syn
+    from oracle import discretization as dz
+    from oracle import exchange as ex
+    cores = len(os.sched_getaffinity(0))
+    dz.FFT_WORKERS = cores
+    w = syn.si_workload(workload)
+    grid = dz.Grid(w["n"], w["cell"], w["ecut"])
+    khat = ex.screened_kernel(grid, w["omega"])
+    M = min(w["n_orb"], 2 * cores)
+    C = syn.initial_coefficients(grid.g2_basis(), M, seed)
+    psi_r = grid.to_real(C)
+    npairs = 0
+    t0 = time.perf_counter()
+    while True:
+        ex.apply_vx_real(psi_r, psi_r[:1], khat, w["alpha"])
+        npairs += M
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": npairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{npairs} pair solves ({M} orbitals x 1 target, repeated) of the FP64 oracle on the "
+                      f"{'x'.join(map(str, w['n']))} grid, scipy.fft with {cores} workers, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    res = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_oracle_pairs_per_s(args.workload, budget_s=8.0, seed=k)
+        if k >= args.warmup:
+            res.append(r)
+    value = statistics.mean(r["value"] for r in res)
+    n_orb = {"si8": 16, "si64": 128, "si216": 432}[args.workload]
+    ms_per_step = pairs_per_exchange(n_orb) / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "note": "each step is a bounded sample of the exchange pair loop"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res[0]["cores"], "kind": "oracle",
+                             "sample": res[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import synthetic as syn
+    import paper_1905_01348_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.load()
+
+    w = syn.si_workload(args.workload, precision=args.precision, fock_mode="ace", seed=rank)
+    params = pkg.make_params(w)
+    n_orb = w["n_orb"]
+    g2 = syn.basis_g2(pkg.pt_basis_indices(params), w["n"], w["cell"])
+    C0 = syn.initial_coefficients(g2, n_orb, seed=rank)
+    pairs = pairs_per_exchange(n_orb)
+
+    sysg = pkg.System(w, C0, device=str(dev))
+    stream = sysg.stream
+    pkg.pt_set_timing(sysg.handle, True)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        sysg.step()
+    pkg.pt_get_timing(sysg.handle, reset=True)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = pkg.pt_launch_count()
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        st, info = sysg.step()
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    launches = pkg.pt_launch_count() - launches0
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    pair_ms, pair_count, groups = pkg.pt_get_timing(sysg.handle, reset=True)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    total_pairs = pairs * args.steps * ws
+    value = total_pairs / (t_ms / 1e3)
+    ms_per_step = t_ms / args.steps
+
+    # roofline of the pair pipeline (F1 + F2 + F3 of every launch group)
+    peaks = measured_peaks()
+    alg_bytes_pair = pair_pipeline_bytes(w["n"], args.precision == "mixed")
+    pair_time_s = pair_ms / 1e3
+    achieved = alg_bytes_pair * pair_count / pair_time_s / 1e9 if pair_time_s > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+            "traffic": traffic_per_launch(args.workload, args.precision),
+            "kernel": "fock pair pipeline (k_fock_f1 + k_fock_f2 + k_fock_f3), one launch group = one round of tiles",
+            "launch_groups": groups, "pair_pipeline_ms": pair_ms,
+            "pairs_per_s_in_pipeline": pair_count / pair_time_s if pair_time_s > 0 else None,
+            "peak_source": peaks["source"]}
+
+    # end to end through the public API with host buffers: upload orbitals,
+    # one step, download orbitals (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(sysg.orbitals()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        nbytes = host_in.numel() * 16
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pkg.pt_set_orbitals(sysg.handle, host_in.numpy())
+            sysg.step()
+            host_out.copy_(torch.from_numpy(sysg.orbitals()))
+        barrier()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([te], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": pairs * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes + 64,
+               "note": "per step: pt_set_orbitals from pinned host memory (orthonormalise + exchange + ACE of the "
+                       "uploaded state), pt_cn_step, pt_get_orbitals to host"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_pairs_per_s(args.workload)
+
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic (seeded random orbitals, relaxed; Gaussian-well Si supercell)",
+            "config": {"workload": args.workload, "grid": list(w["n"]), "n_orb": n_orb,
+                       "pairs_per_step": pairs, "fock_mode": "ace", "precision": args.precision,
+                       "scf_tol": w["scf_tol"], "dt_au": w["dt"],
+                       "l2": "inputs larger than L2 (orbitals and pair intermediates are GBs)",
+                       "parallelism": f"replicas x{ws}"},
+            "wall_s_per_fs": ms_per_step * STEPS_PER_FS / 1e3,
+            "scf_iters": [i["scf_iters"] for i in infos],
+            "converged": [bool(i["converged"]) for i in infos],
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sysg.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

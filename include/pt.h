@@ -145,6 +145,19 @@ pt_status pt_observables(pt_system* s, double* energy, double* dipole);
 /* Device pointer of the current orbitals (npw x n_orb complex128). */
 pt_status pt_orbitals_device(pt_system* s, void** d_psi);
 
+/* Timing of the exchange pair pipeline (the three pair kernels of every
+ * exchange application, Eq. 3): when enabled, CUDA events are recorded on the
+ * system's stream around each application's pair kernels (one extra
+ * synchronisation per application). pt_get_timing returns the accumulated
+ * milliseconds, unordered pairs solved and pair-kernel launch groups since
+ * the last reset; reset clears them. */
+pt_status pt_set_timing(pt_system* s, int enable);
+pt_status pt_get_timing(pt_system* s, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * systems); differences of two readings count the launches in between. */
+pt_status pt_launch_count(uint64_t* count);
+
 /* Release the handle (the workspace stays owned by the caller). */
 pt_status pt_destroy(pt_system* s);
 

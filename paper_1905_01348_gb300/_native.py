@@ -98,6 +98,9 @@ def load() -> C.CDLL:
         "pt_set_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
         "pt_observables": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "pt_orbitals_device": (C.c_int, [vp, C.POINTER(vp)]),
+        "pt_set_timing": (C.c_int, [vp, C.c_int]),
+        "pt_get_timing": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]),
+        "pt_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
         "pt_destroy": (C.c_int, [vp]),
         "pt_last_error": (C.c_char_p, [vp]),
     }
@@ -227,6 +230,24 @@ def pt_orbitals_device(h) -> int:
     p = C.c_void_p()
     _check(load().pt_orbitals_device(h, C.byref(p)), h)
     return p.value
+
+
+def pt_set_timing(h, enable: bool) -> None:
+    _check(load().pt_set_timing(h, int(bool(enable))), h)
+
+
+def pt_get_timing(h, reset: bool = False) -> tuple[float, int, int]:
+    ms = C.c_double(0.0)
+    pairs = C.c_int64(0)
+    groups = C.c_int64(0)
+    _check(load().pt_get_timing(h, C.byref(ms), C.byref(pairs), C.byref(groups), int(bool(reset))), h)
+    return ms.value, pairs.value, groups.value
+
+
+def pt_launch_count() -> int:
+    n = C.c_uint64(0)
+    _check(load().pt_launch_count(C.byref(n)))
+    return n.value
 
 
 def pt_destroy(h) -> None:

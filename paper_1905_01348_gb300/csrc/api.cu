@@ -82,6 +82,11 @@ struct pt_system {
   double energy = 0.0, dipole[3] = {0, 0, 0};
   int and_count = 0;
   std::vector<int> and_order;
+  // pair-pipeline timing
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double t_pair_ms = 0.0;
+  long long t_pairs = 0, t_groups = 0;
 };
 
 static std::string g_last_error = "no error";
@@ -311,7 +316,17 @@ static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
   PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * sys->N * sys->ne, sys->s));
   const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
   const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
+  if (sys->timing) PT_CK(cudaEventRecord(sys->ev0, sys->s));
   PT_CK(pt::fock_pairs<T>(pr, nullptr, sys->w_r, nullptr, sys->plan_sym, 1, sys->g, kt, sys->scratch, sys->tw, sys->s));
+  if (sys->timing) {
+    PT_CK(cudaEventRecord(sys->ev1, sys->s));
+    PT_CK(cudaEventSynchronize(sys->ev1));
+    float ms = 0.f;
+    PT_CK(cudaEventElapsedTime(&ms, sys->ev0, sys->ev1));
+    sys->t_pair_ms += ms;
+    sys->t_pairs += (long long)sys->ne * (sys->ne + 1) / 2;
+    sys->t_groups += sys->plan_sym.n_launch;
+  }
   return to_basis<T>(sys, sys->w_r, sys->ne, out, accumulate, nullptr, nullptr);
 }
 
@@ -837,8 +852,35 @@ pt_status pt_orbitals_device(pt_system* sys, void** d_psi) {
   return PT_OK;
 }
 
+pt_status pt_set_timing(pt_system* sys, int enable) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  if (enable && sys->ev0 == nullptr) {
+    PT_CK(cudaEventCreate(&sys->ev0));
+    PT_CK(cudaEventCreate(&sys->ev1));
+  }
+  sys->timing = enable != 0;
+  return PT_OK;
+}
+
+pt_status pt_get_timing(pt_system* sys, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  if (pair_ms) *pair_ms = sys->t_pair_ms;
+  if (pairs) *pairs = sys->t_pairs;
+  if (launch_groups) *launch_groups = sys->t_groups;
+  if (reset) { sys->t_pair_ms = 0.0; sys->t_pairs = 0; sys->t_groups = 0; }
+  return PT_OK;
+}
+
+pt_status pt_launch_count(uint64_t* count) {
+  if (count == nullptr) return PT_ERR_INVALID;
+  *count = (uint64_t)pt::launch_count();
+  return PT_OK;
+}
+
 pt_status pt_destroy(pt_system* sys) {
   if (sys == nullptr) return PT_OK;
+  if (sys->ev0) cudaEventDestroy(sys->ev0);
+  if (sys->ev1) cudaEventDestroy(sys->ev1);
   std::free(sys->plan_sym.launch_first);
   std::free(sys->plan_sym.launch_count);
   std::free(sys->plan_x.launch_first);

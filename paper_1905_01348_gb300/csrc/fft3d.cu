@@ -7,8 +7,9 @@
 // The axis-0 pass can fuse "inverse, multiply by a real field, forward"
 // (local potential times orbital) or "forward, multiply by a reciprocal-space
 // factor, inverse" (Hartree solve), so those operations cost no extra pass.
-#include <cmath>
 #include <algorithm>
+#include <atomic>
+#include <cmath>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -139,6 +140,7 @@ cudaError_t fft_rows(const void* in, void* out, long nvol, Grid3 g, int inverse,
   else
     k_rows<T, false><<<(unsigned)nblk, nthr, smem, s>>>((const C*)in, (C*)out, nrows, L, rpc, tw_for<T>(tw, L), sc,
                                                        mul_real, rpv);
+  launched();
   return cudaGetLastError();
 }
 
@@ -166,6 +168,7 @@ cudaError_t fft_cols(void* data, long nvol, Grid3 g, int axis, int inverse, int 
     PT_COLS(false, 2);  // forward, multiply, inverse
   }
 #undef PT_COLS
+  launched();
   return cudaGetLastError();
 }
 
@@ -206,7 +209,7 @@ cudaError_t scatter_basis(const double2* in, long in_ld, void* out, long nvol, G
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(C) * g.N() * nvol, s);
   if (e != cudaSuccess) return e;
   dim3 grid((npw + 255) / 256, (unsigned)nvol);
-  k_scatter<T><<<grid, 256, 0, s>>>(in, in_ld, (C*)out, g.N(), basis, npw, scale);
+  k_scatter<T><<<grid, 256, 0, s>>>(in, in_ld, (C*)out, g.N(), basis, npw, scale); launched();
   return cudaGetLastError();
 }
 
@@ -215,7 +218,7 @@ cudaError_t gather_basis(const void* in, double2* out, long out_ld, long nvol, G
                          double scale, const double* kin, const double2* x, long x_ld, int accumulate, cudaStream_t s) {
   using C = cplx<T>;
   dim3 grid((npw + 255) / 256, (unsigned)nvol);
-  k_gather<T><<<grid, 256, 0, s>>>((const C*)in, out, out_ld, g.N(), basis, npw, scale, kin, x, x_ld, accumulate);
+  k_gather<T><<<grid, 256, 0, s>>>((const C*)in, out, out_ld, g.N(), basis, npw, scale, kin, x, x_ld, accumulate); launched();
   return cudaGetLastError();
 }
 
@@ -226,7 +229,7 @@ __global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict
 
 cudaError_t convert_c128_to_c64(const double2* in, float2* out, long n, cudaStream_t s) {
   long blocks = std::min<long>((n + 255) / 256, 152L * 32);
-  k_c128_to_c64<<<(unsigned)std::max<long>(blocks, 1), 256, 0, s>>>(in, out, n);
+  k_c128_to_c64<<<(unsigned)std::max<long>(blocks, 1), 256, 0, s>>>(in, out, n); launched();
   return cudaGetLastError();
 }
 
@@ -239,6 +242,10 @@ template cudaError_t scatter_basis<float>(const double2*, long, void*, long, Gri
 template cudaError_t scatter_basis<double>(const double2*, long, void*, long, Grid3, const int*, int, double, cudaStream_t);
 template cudaError_t gather_basis<float>(const void*, double2*, long, long, Grid3, const int*, int, double, const double*, const double2*, long, int, cudaStream_t);
 template cudaError_t gather_basis<double>(const void*, double2*, long, long, Grid3, const int*, int, double, const double*, const double2*, long, int, cudaStream_t);
+
+static std::atomic<unsigned long long> g_launches{0};
+void launched(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 std::string cuda_msg(cudaError_t e) { return std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e); }
 

@@ -212,11 +212,11 @@ cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_
     const int t0 = plan.launch_first[l], nt = plan.launch_count[l];
     dim3 g13((unsigned)(g.n0 * (g.n1 / rr)), (unsigned)nt);
     k_fock_f1<T><<<g13, thr13, smem13, s>>>((const C*)psi_r, (const C*)x_r, plan.d_tiles, t0, X, g.n0, g.n1, g.n2, rr,
-                                           tw2);
+                                           tw2); launched();
     dim3 g2((unsigned)g.n2, (unsigned)(nt * kTileMax * kTileMax));
-    k_fock_f2<T><<<g2, thr2, smem2, s>>>(X, plan.d_tiles, t0, g.n0, g.n1, g.n2, khat_t, tw0, tw1);
+    k_fock_f2<T><<<g2, thr2, smem2, s>>>(X, plan.d_tiles, t0, g.n0, g.n1, g.n2, khat_t, tw0, tw1); launched();
     k_fock_f3<T><<<g13, thr13, smem13, s>>>((const C*)psi_r, (const C*)x_r, (C*)w_occ, (C*)w_x, plan.d_tiles, t0, X,
-                                           g.n0, g.n1, g.n2, rr, sym, tw2);
+                                           g.n0, g.n1, g.n2, rr, sym, tw2); launched();
   }
   return cudaGetLastError();
 }

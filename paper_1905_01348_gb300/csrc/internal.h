@@ -103,4 +103,8 @@ cudaError_t reduce_norm2(const double2* x, long n, double* partials, int npart, 
 
 std::string cuda_msg(cudaError_t e);
 
+// Count of kernels this library has launched (all systems, this process).
+void launched(int n = 1);
+unsigned long long launch_count();
+
 }  // namespace pt

@@ -56,7 +56,7 @@ __global__ void k_density(const double2* __restrict__ psi_r, long N, int ne, dou
 }
 
 cudaError_t density(const double2* psi_r, long N, int ne, double* rho, cudaStream_t s) {
-  k_density<<<nblk(N, 256, 152L * 64), 256, 0, s>>>(psi_r, N, ne, rho);
+  k_density<<<nblk(N, 256, 152L * 64), 256, 0, s>>>(psi_r, N, ne, rho); launched();
   return cudaGetLastError();
 }
 
@@ -81,13 +81,13 @@ __global__ void k_vloc(const double* __restrict__ vion, const double2* __restric
 }
 
 cudaError_t rho_to_complex(const double* rho, double2* buf, long N, cudaStream_t s) {
-  k_rho_to_complex<<<nblk(N, 256), 256, 0, s>>>(rho, buf, N);
+  k_rho_to_complex<<<nblk(N, 256), 256, 0, s>>>(rho, buf, N); launched();
   return cudaGetLastError();
 }
 
 cudaError_t assemble_vloc(const double* vion, const double2* vh_c, const double* rho, long N, int use_h, double w_lda,
                           double* vh, double* vloc, cudaStream_t s) {
-  k_vloc<<<nblk(N, 256), 256, 0, s>>>(vion, vh_c, rho, N, use_h, w_lda, vh, vloc);
+  k_vloc<<<nblk(N, 256), 256, 0, s>>>(vion, vh_c, rho, N, use_h, w_lda, vh, vloc); launched();
   return cudaGetLastError();
 }
 
@@ -128,7 +128,7 @@ cudaError_t ion_potential(double* v, Grid3 g, const double* cell, const double* 
   // exp(-d^2 / (2 sigma^2)) < 1e-20 beyond rcut
   const double rcut = sigma * std::sqrt(2.0 * 46.0);
   k_vion<<<nblk(g.N(), 128, 152L * 64), 128, 0, s>>>(v, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2], d_atoms, na,
-                                                     depth, sigma, rcut);
+                                                     depth, sigma, rcut); launched();
   return cudaGetLastError();
 }
 
@@ -144,7 +144,7 @@ __global__ void k_half_step(const double2* __restrict__ psi, const double2* __re
 }
 
 cudaError_t half_step(const double2* psi, const double2* R, double hdt, double2* out, long n, cudaStream_t s) {
-  k_half_step<<<nblk(n, 256), 256, 0, s>>>(psi, R, hdt, out, n);
+  k_half_step<<<nblk(n, 256), 256, 0, s>>>(psi, R, hdt, out, n); launched();
   return cudaGetLastError();
 }
 
@@ -165,8 +165,8 @@ __global__ void k_resid(const double2* __restrict__ psi_f, const double2* __rest
 cudaError_t pt_residual(const double2* psi_f, const double2* T, const double2* ph, double hdt, double2* r, long n,
                         double* part, double* out_norm2, cudaStream_t s) {
   const unsigned b = nblk(n, 256, 1024);
-  k_resid<<<b, 256, 0, s>>>(psi_f, T, ph, hdt, r, n, part);
-  k_finalize<<<1, 32, 0, s>>>(part, b, 1, out_norm2);
+  k_resid<<<b, 256, 0, s>>>(psi_f, T, ph, hdt, r, n, part); launched();
+  k_finalize<<<1, 32, 0, s>>>(part, b, 1, out_norm2); launched();
   return cudaGetLastError();
 }
 
@@ -184,7 +184,7 @@ __global__ void k_precond_step(double2* __restrict__ x, const double2* __restric
 }
 
 cudaError_t precond_step(double2* x, const double2* R, const double* kin, int npw, long n, double tau, cudaStream_t s) {
-  k_precond_step<<<nblk(n, 256), 256, 0, s>>>(x, R, kin, npw, n, tau);
+  k_precond_step<<<nblk(n, 256), 256, 0, s>>>(x, R, kin, npw, n, tau); launched();
   return cudaGetLastError();
 }
 
@@ -207,7 +207,7 @@ __global__ void k_anderson_push(const double2* __restrict__ x, const double2* __
 
 cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, double2* dx, double2* dr,
                           long n, int have_prev, cudaStream_t s) {
-  k_anderson_push<<<nblk(n, 256), 256, 0, s>>>(x, r, xp, rp, dx, dr, n, have_prev);
+  k_anderson_push<<<nblk(n, 256), 256, 0, s>>>(x, r, xp, rp, dx, dr, n, have_prev); launched();
   return cudaGetLastError();
 }
 
@@ -274,7 +274,7 @@ __global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride
 cudaError_t anderson_dots(const double2* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
                           int npw, int ne, int mdim, double2* gram, double2* rhs, cudaStream_t s) {
   if (sl.k > kSlotMax) return cudaErrorInvalidValue;
-  k_anderson_dots<<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
+  k_anderson_dots<<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs); launched();
   return cudaGetLastError();
 }
 
@@ -335,7 +335,7 @@ __global__ void k_anderson_solve(const double2* __restrict__ gram, const double2
 
 cudaError_t anderson_solve(const double2* gram, const double2* rhs, const SlotList& sl, int mdim, int ne,
                            double2* gamma, cudaStream_t s) {
-  k_anderson_solve<<<(ne + 63) / 64, 64, 0, s>>>(gram, rhs, sl, mdim, ne, gamma);
+  k_anderson_solve<<<(ne + 63) / 64, 64, 0, s>>>(gram, rhs, sl, mdim, ne, gamma); launched();
   return cudaGetLastError();
 }
 
@@ -366,7 +366,7 @@ __global__ void k_anderson_update(double2* __restrict__ x, const double2* __rest
 cudaError_t anderson_update(double2* x, const double2* r, const double2* dX, const double2* dR, long slot_stride,
                             const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta,
                             cudaStream_t s) {
-  k_anderson_update<<<nblk(n, 256), 256, 0, s>>>(x, r, dX, dR, slot_stride, sl, gamma, mdim, npw, n, beta);
+  k_anderson_update<<<nblk(n, 256), 256, 0, s>>>(x, r, dX, dR, slot_stride, sl, gamma, mdim, npw, n, beta); launched();
   return cudaGetLastError();
 }
 
@@ -380,8 +380,8 @@ __global__ void k_drho(const double* __restrict__ a, const double* __restrict__ 
 
 cudaError_t rho_change(const double* a, const double* b, long N, double* part, double* out, cudaStream_t s) {
   const unsigned nb = nblk(N, 256, 1024);
-  k_drho<<<nb, 256, 0, s>>>(a, b, N, part);
-  k_finalize<<<1, 32, 0, s>>>(part, nb, 1, out);
+  k_drho<<<nb, 256, 0, s>>>(a, b, N, part); launched();
+  k_finalize<<<1, 32, 0, s>>>(part, nb, 1, out); launched();
   return cudaGetLastError();
 }
 
@@ -429,13 +429,13 @@ cudaError_t energy_sums(const double* rho, const double* vion, const double* vh,
                         const double2* c, const double* kin, int npw, int ne, const double2* negM, double* part,
                         double* out8, cudaStream_t s) {
   const unsigned nb = nblk(g.N(), 256, 1024);
-  k_grid_sums<<<nb, 256, 0, s>>>(rho, vion, vh, use_h, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2], part);
-  k_finalize<<<1, 32, 0, s>>>(part, nb, 6, out8);
+  k_grid_sums<<<nb, 256, 0, s>>>(rho, vion, vh, use_h, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2], part); launched();
+  k_finalize<<<1, 32, 0, s>>>(part, nb, 6, out8); launched();
   const long n = (long)npw * ne;
   const unsigned nb2 = nblk(n, 256, 1024);
-  k_kin_sum<<<nb2, 256, 0, s>>>(c, kin, npw, n, part + 6 * 1024);
-  k_finalize<<<1, 32, 0, s>>>(part + 6 * 1024, nb2, 1, out8 + 6);
-  if (negM != nullptr) k_trace_real<<<1, 32, 0, s>>>(negM, ne, out8 + 7);
+  k_kin_sum<<<nb2, 256, 0, s>>>(c, kin, npw, n, part + 6 * 1024); launched();
+  k_finalize<<<1, 32, 0, s>>>(part + 6 * 1024, nb2, 1, out8 + 6); launched();
+  if (negM != nullptr) { k_trace_real<<<1, 32, 0, s>>>(negM, ne, out8 + 7); launched(); }
   return cudaGetLastError();
 }
 
@@ -455,7 +455,7 @@ __global__ void k_hartree_factor(double* __restrict__ f, int n0, int n1, int n2,
 }
 
 cudaError_t hartree_factor(double* f, Grid3 g, const double* cell, cudaStream_t s) {
-  k_hartree_factor<<<nblk(g.N(), 256), 256, 0, s>>>(f, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2]);
+  k_hartree_factor<<<nblk(g.N(), 256), 256, 0, s>>>(f, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2]); launched();
   return cudaGetLastError();
 }
 
@@ -467,7 +467,7 @@ __global__ void k_copy_scaled(const double2* __restrict__ a, double2* __restrict
 }
 
 cudaError_t copy_scaled(const double2* a, double2* b, long n, double sc, cudaStream_t s) {
-  k_copy_scaled<<<nblk(n, 256), 256, 0, s>>>(a, b, n, sc);
+  k_copy_scaled<<<nblk(n, 256), 256, 0, s>>>(a, b, n, sc); launched();
   return cudaGetLastError();
 }
 
@@ -486,7 +486,7 @@ __global__ void k_axpy(double2 a, const double2* __restrict__ x, double2* __rest
 }
 
 cudaError_t axpy(double2 a, const double2* x, double2* y, long n, cudaStream_t s) {
-  k_axpy<<<nblk(n, 256), 256, 0, s>>>(a, x, y, n);
+  k_axpy<<<nblk(n, 256), 256, 0, s>>>(a, x, y, n); launched();
   return cudaGetLastError();
 }
 

@@ -156,12 +156,12 @@ cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const dou
   if (K == 0) { ksplit = 1; kchunk = GBK; }
   dim3 grid(tm, tn, (unsigned)(batch * ksplit));
   k_gemm<Tc><<<grid, 256, 0, s>>>(opA, opB, M, N, K, kchunk, ksplit, alpha, A, lda, strideA, B, ldb, strideB, beta, C,
-                                  ldc, strideC, ws);
+                                  ldc, strideC, ws); launched();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || ksplit == 1) return e;
   const long total = (long)batch * M * N;
   const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
-  k_splitk_reduce<<<blocks, 256, 0, s>>>(M, N, batch, ksplit, alpha, ws, beta, C, ldc, strideC);
+  k_splitk_reduce<<<blocks, 256, 0, s>>>(M, N, batch, ksplit, alpha, ws, beta, C, ldc, strideC); launched();
   return cudaGetLastError();
 }
 
@@ -217,10 +217,10 @@ cudaError_t cholesky(double2* A, int n, int* d_status, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   for (int j = 0; j < n; ++j) {
-    k_chol_pivot<<<1, 256, 0, s>>>(A, n, j, d_status);
-    if (j + 1 < n) k_chol_update<<<n - j - 1, 128, 0, s>>>(A, n, j, d_status);
+    k_chol_pivot<<<1, 256, 0, s>>>(A, n, j, d_status); launched();
+    if (j + 1 < n) { k_chol_update<<<n - j - 1, 128, 0, s>>>(A, n, j, d_status); launched(); }
   }
-  k_zero_upper<<<std::max(1, std::min(1024, (n * n + 255) / 256)), 256, 0, s>>>(A, n);
+  k_zero_upper<<<std::max(1, std::min(1024, (n * n + 255) / 256)), 256, 0, s>>>(A, n); launched();
   return cudaGetLastError();
 }
 
@@ -251,7 +251,7 @@ __global__ void k_tri_inverse(const double2* __restrict__ L, double2* __restrict
 }
 
 cudaError_t tri_inverse(const double2* L, double2* Linv, int n, cudaStream_t s) {
-  k_tri_inverse<<<n, 128, sizeof(double2) * n, s>>>(L, Linv, n);
+  k_tri_inverse<<<n, 128, sizeof(double2) * n, s>>>(L, Linv, n); launched();
   return cudaGetLastError();
 }
 

@@ -110,3 +110,16 @@ def gaussian_vectors(shape, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(int(seed)))
     z = rng.standard_normal(tuple(shape) + (2,))
     return z[..., 0] + 1j * z[..., 1]
+
+
+def basis_g2(flat_index: np.ndarray, n, cell) -> np.ndarray:
+    """|G|^2 of grid frequencies given by row-major flat indices (input-envelope helper)."""
+    flat = np.asarray(flat_index, dtype=np.int64)
+    idx = np.unravel_index(flat, tuple(int(v) for v in n))
+    out = np.zeros(flat.shape, dtype=np.float64)
+    for k in range(3):
+        nk = int(n[k])
+        m = np.where(idx[k] < (nk + 1) // 2, idx[k], idx[k] - nk)
+        g = 2.0 * np.pi * m / float(cell[k])
+        out += g * g
+    return out
