@@ -76,6 +76,8 @@ typedef struct pt_params {
   int use_lda;           /* 1: include (1 - alpha) Slater exchange */
   int relax_iters;       /* start-state relaxation steps (steepest descent on H_loc) */
   double relax_tau;      /* relaxation step length */
+  double relax_mix;      /* Kerker mixing weight b of the relaxation density */
+  double relax_q0;       /* Kerker wavevector q0 (bohr^-1): weight b |G|^2 / (|G|^2 + q0^2) */
   int pair_tile;         /* orbitals per pair-tile edge (0 = automatic) */
 } pt_params;
 
@@ -102,9 +104,11 @@ pt_status pt_workspace_size(const pt_params* p, size_t* bytes);
 
 /* Create a system (Eq. 5 state). psi0_host: n_orb x npw complex128 initial
  * coefficients (need not be orthonormal). They are orthonormalised by
- * Cholesky (Sec. 3.4), relaxed by relax_iters steepest-descent steps on the
- * local Hamiltonian, and the exchange data of the start state (W = V_X Psi,
- * and ACE when fock_mode is PT_FOCK_ACE) are built. Synchronises the stream. */
+ * Cholesky (Sec. 3.4), relaxed by relax_iters preconditioned steepest-descent
+ * steps on the local Hamiltonian of a Kerker-mixed density (a stand-in for
+ * the ground state the paper starts from), and the exchange data of the
+ * start state (W = V_X Psi, and ACE when fock_mode is PT_FOCK_ACE) are
+ * built. Synchronises the stream. */
 pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_workspace,
                          size_t workspace_bytes, void* stream, pt_system** out);
 

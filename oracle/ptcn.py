@@ -44,7 +44,11 @@ Readings (the paper is silent on these details):
   Hamiltonian (no Fock term):
       Psi <- orth(Psi - tau P (H_loc Psi - Psi (Psi^H H_loc Psi))),
       P = diag 1 / (1 + |G + kappa|^2 / 2),
-  H_loc rebuilt from the density of Psi each step.
+  with H_loc built from a Kerker-mixed density
+      rho_mix <- rho_mix + F^{-1}[ b |G|^2 / (|G|^2 + q0^2) F[rho(Psi) - rho_mix] ],
+  rho_mix starting at rho(Psi_0) (b = relax_mix, q0 = relax_q0). Without
+  the mixing the long-wavelength Hartree response (4 pi / |G|^2, growing with
+  the cell) makes the descent unstable in the 3x3x3 supercell.
 """
 from __future__ import annotations
 
@@ -81,6 +85,8 @@ class Params:
     use_lda: bool = True
     relax_iters: int = 40
     relax_tau: float = 1.0
+    relax_mix: float = 0.5
+    relax_q0: float = 1.0
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -155,9 +161,16 @@ class Model:
     # -- state ----------------------------------------------------------------
     def relax(self, Psi: np.ndarray, iters: int, tau: float) -> np.ndarray:
         """Preconditioned steepest descent on the local Hamiltonian (start-state reading above)."""
+        from .discretization import fftn, ifftn
         prec = (1.0 / (1.0 + self.local.kin))[:, None]
+        g2 = self.grid.g2
+        q2 = self.p.relax_q0 ** 2
+        kerker = self.p.relax_mix * g2 / (g2 + q2)
+        rho_mix = self.density(Psi)
         for _ in range(int(iters)):
-            HP = self.local.apply_local(self.local.local_potential(self.density(Psi)), Psi)
+            rho = self.density(Psi)
+            rho_mix = rho_mix + np.real(ifftn(kerker * fftn((rho - rho_mix).astype(complex))))
+            HP = self.local.apply_local(self.local.local_potential(rho_mix), Psi)
             R = HP - Psi @ (Psi.conj().T @ HP)
             Psi = orthonormalize(Psi - tau * prec * R)
         return Psi

@@ -46,6 +46,8 @@ class PtParams(C.Structure):
         ("use_lda", C.c_int),
         ("relax_iters", C.c_int),
         ("relax_tau", C.c_double),
+        ("relax_mix", C.c_double),
+        ("relax_q0", C.c_double),
         ("pair_tile", C.c_int),
     ]
 
@@ -149,6 +151,8 @@ def make_params(d: dict) -> PtParams:
     p.use_lda = int(bool(d.get("use_lda", True)))
     p.relax_iters = int(d.get("relax_iters", 40))
     p.relax_tau = float(d.get("relax_tau", 1.0))
+    p.relax_mix = float(d.get("relax_mix", 0.5))
+    p.relax_q0 = float(d.get("relax_q0", 1.0))
     p.pair_tile = int(d.get("pair_tile", 0))
     return p
 

@@ -58,7 +58,7 @@ struct pt_system {
   float2* tw32 = nullptr;
   double* khat64 = nullptr;
   float* khat32 = nullptr;
-  double *hfac = nullptr, *vion = nullptr, *vloc = nullptr, *vh = nullptr, *rho = nullptr, *rho2 = nullptr;
+  double *hfac = nullptr, *kfac = nullptr, *rho_mix = nullptr, *vion = nullptr, *vloc = nullptr, *vh = nullptr, *rho = nullptr, *rho2 = nullptr;
   double* d_atoms = nullptr;
   double2 *psi = nullptr, *psi_half = nullptr, *psi_f = nullptr, *hpsi = nullptr, *tmp = nullptr, *rbuf = nullptr;
   double2 *wg = nullptr, *xi = nullptr, *xprev = nullptr, *rprev = nullptr, *dX = nullptr, *dR = nullptr;
@@ -187,6 +187,8 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   t->tw32 = c.take<float2>(pt::kTwiddleTotal);
   if (mixed) t->khat32 = c.take<float>(N); else t->khat64 = c.take<double>(N);
   t->hfac = c.take<double>(N);
+  t->kfac = c.take<double>(N);
+  t->rho_mix = c.take<double>(N);
   t->vion = c.take<double>(N);
   t->vloc = c.take<double>(N);
   t->vh = c.take<double>(N);
@@ -261,10 +263,10 @@ static pt_status real_orbitals(pt_system* sys, const double2* c) {
   return PT_OK;
 }
 
-static pt_status local_potential(pt_system* sys) {
+static pt_status local_potential(pt_system* sys, const double* rho) {
   const int use_h = sys->p.use_hartree ? 1 : 0;
   if (use_h) {
-    PT_CK(pt::rho_to_complex(sys->rho, sys->hbuf, sys->N, sys->s));
+    PT_CK(pt::rho_to_complex(rho, sys->hbuf, sys->N, sys->s));
     PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, 1, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
     PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
     PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 0, 0, 2, 1.0, sys->hfac, sys->tw, sys->s));
@@ -272,7 +274,21 @@ static pt_status local_potential(pt_system* sys) {
     PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, 1, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
   }
   const double w_lda = sys->p.use_lda ? (1.0 - sys->p.alpha) : 0.0;
-  PT_CK(pt::assemble_vloc(sys->vion, sys->hbuf, sys->rho, sys->N, use_h, w_lda, sys->vh, sys->vloc, sys->s));
+  PT_CK(pt::assemble_vloc(sys->vion, sys->hbuf, rho, sys->N, use_h, w_lda, sys->vh, sys->vloc, sys->s));
+  return PT_OK;
+}
+
+static pt_status local_potential(pt_system* sys) { return local_potential(sys, sys->rho); }
+
+// rho_mix += F^-1[ b |G|^2/(|G|^2 + q0^2) F[rho - rho_mix] ]
+static pt_status kerker_mix(pt_system* sys) {
+  PT_CK(pt::diff_to_complex(sys->rho, sys->rho_mix, sys->hbuf, sys->N, sys->s));
+  PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, 1, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 0, 0, 2, 1.0, sys->kfac, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<double>(sys->hbuf, 1, sys->g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_rows<double>(sys->hbuf, sys->hbuf, 1, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::add_real(sys->hbuf, sys->rho_mix, sys->N, sys->s));
   return PT_OK;
 }
 
@@ -468,10 +484,15 @@ static pt_status observables(pt_system* sys) {
 static pt_status relax(pt_system* sys) {
   const int ne = sys->ne, npw = sys->npw;
   const long n = (long)npw * ne;
+  if (sys->p.relax_iters > 0) {
+    PT_TRY(real_orbitals(sys, sys->psi));
+    PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho_mix, sys->s));
+  }
   for (int k = 0; k < sys->p.relax_iters; ++k) {
     PT_TRY(real_orbitals(sys, sys->psi));
     PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho, sys->s));
-    PT_TRY(local_potential(sys));
+    PT_TRY(kerker_mix(sys));
+    PT_TRY(local_potential(sys, sys->rho_mix));
     PT_TRY(apply_local_from_real(sys, sys->psi, sys->hpsi));
     PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->psi, npw, sys->hpsi, npw, kZero, sys->S, ne));
     PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->psi, npw, sys->S, ne, kOne, sys->hpsi, npw));
@@ -698,6 +719,7 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   PT_CK(cudaStreamSynchronize(s));
   // device tables
   PT_CK(pt::hartree_factor(sys->hfac, sys->g, p->cell, s));
+  PT_CK(pt::kerker_factor(sys->kfac, sys->g, p->cell, p->relax_mix, p->relax_q0, s));
   if (p->n_atoms > 0)
     PT_CK(pt::ion_potential(sys->vion, sys->g, p->cell, sys->d_atoms, p->n_atoms, p->well_depth, p->well_sigma, s));
   else

@@ -183,6 +183,10 @@ template <typename T>
 cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
                        Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s) {
   using C = cplx<T>;
+  if constexpr (sizeof(T) == 4) {
+    if (fock_fast_supported(g))
+      return fock_pairs_fast(psi_r, x_r, w_occ, w_x, plan, g, khat_t, scratch, twp<float>(tw, g.n0), s);
+  }
   const bool fp64 = sizeof(T) == 8;
   const int rr = rows_per_block(g.n1, fp64);
   const int rowlen = rr * g.n2;
@@ -251,6 +255,17 @@ int fock_build_tiles(int n_occ, int n_x, int tile, int sym, int tiles_per_launch
     } else {
       for (int a = 0; a < a_n; ++a)
         for (int b = 0; b < b_n; ++b) { t.pi[t.n_pairs] = (signed char)a; t.pj[t.n_pairs] = (signed char)(a_n + b); ++t.n_pairs; }
+    }
+    for (int o = 0; o < t.n_orb; ++o) {
+      if (!t.is_out[o]) continue;
+      int c = 0;
+      for (int q = 0; q < t.n_pairs; ++q) {
+        if (t.pj[q] == o) { t.out_pair[o][c] = (signed char)q; t.out_other[o][c] = t.pi[q]; t.out_conj[o][c] = 0; ++c; }
+        if (sym && t.pi[q] == o && t.pi[q] != t.pj[q]) {
+          t.out_pair[o][c] = (signed char)q; t.out_other[o][c] = t.pj[q]; t.out_conj[o][c] = 1; ++c;
+        }
+      }
+      t.out_n[o] = (signed char)c;
     }
     tiles.push_back(t);
     return (int)tiles.size() - 1;

@@ -60,6 +60,13 @@ struct PairTile {
   signed char is_out[2 * kTileMax];  // accumulate into this orbital's W
   signed char pi[kTileMax * kTileMax];
   signed char pj[kTileMax * kTileMax];
+  // contributions to each output orbital: pair index, the other orbital's
+  // slot, and whether the pair potential enters conjugated (i side of a
+  // symmetric pair). At most kTileMax per output.
+  signed char out_n[2 * kTileMax];
+  signed char out_pair[2 * kTileMax][kTileMax];
+  signed char out_other[2 * kTileMax][kTileMax];
+  signed char out_conj[2 * kTileMax][kTileMax];
 };
 
 struct FockPlan {
@@ -77,6 +84,10 @@ template <typename T>
 cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
                        Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s);
 size_t fock_scratch_elems(const FockPlan& plan, Grid3 g);
+// FP32 cubic fast path (fock_fast.cu): n0 == n1 == n2 in {32, 64, 96}.
+bool fock_fast_supported(Grid3 g);
+cudaError_t fock_pairs_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, Grid3 g,
+                            const float* khat_t, void* scratch, const float2* tw_L, cudaStream_t s);
 // Host tile schedules. sym: pairs i <= j of n_occ orbitals; otherwise n_occ x n_x pairs.
 int fock_build_tiles(int n_occ, int n_x, int tile, int sym, int tiles_per_launch, PairTile** tiles_out,
                      int** launch_first, int** launch_count, int* n_launch);

@@ -491,3 +491,51 @@ cudaError_t axpy(double2 a, const double2* x, double2* y, long n, cudaStream_t s
 }
 
 }  // namespace pt
+
+namespace pt {
+
+__global__ void k_diff_to_complex(const double* __restrict__ a, const double* __restrict__ b, double2* __restrict__ buf,
+                                  long N) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x)
+    buf[t] = make_double2(a[t] - b[t], 0.0);
+}
+
+__global__ void k_add_real(const double2* __restrict__ buf, double* __restrict__ a, long N) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x)
+    a[t] += buf[t].x;
+}
+
+cudaError_t diff_to_complex(const double* a, const double* b, double2* buf, long N, cudaStream_t s) {
+  k_diff_to_complex<<<nblk(N, 256), 256, 0, s>>>(a, b, buf, N); launched();
+  return cudaGetLastError();
+}
+
+cudaError_t add_real(const double2* buf, double* a, long N, cudaStream_t s) {
+  k_add_real<<<nblk(N, 256), 256, 0, s>>>(buf, a, N); launched();
+  return cudaGetLastError();
+}
+
+// b |G|^2 / (|G|^2 + q0^2) / N  (Kerker weight with the inverse-FFT normalisation)
+__global__ void k_kerker_factor(double* __restrict__ f, int n0, int n1, int n2, double a0, double a1, double a2,
+                                double b, double q2) {
+  const long N = (long)n0 * n1 * n2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x) {
+    const int i2 = (int)(t % n2);
+    const int i1 = (int)((t / n2) % n1);
+    const int i0 = (int)(t / ((long)n1 * n2));
+    const int m0 = i0 < (n0 + 1) / 2 ? i0 : i0 - n0;
+    const int m1 = i1 < (n1 + 1) / 2 ? i1 : i1 - n1;
+    const int m2 = i2 < (n2 + 1) / 2 ? i2 : i2 - n2;
+    const double g0 = 2.0 * M_PI * m0 / a0, g1 = 2.0 * M_PI * m1 / a1, g2 = 2.0 * M_PI * m2 / a2;
+    const double gg = g0 * g0 + g1 * g1 + g2 * g2;
+    f[t] = b * gg / (gg + q2) / (double)N;
+  }
+}
+
+cudaError_t kerker_factor(double* f, Grid3 g, const double* cell, double b, double q0, cudaStream_t s) {
+  k_kerker_factor<<<nblk(g.N(), 256), 256, 0, s>>>(f, g.n0, g.n1, g.n2, cell[0], cell[1], cell[2], b, q0 * q0);
+  launched();
+  return cudaGetLastError();
+}
+
+}  // namespace pt

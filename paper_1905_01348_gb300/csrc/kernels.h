@@ -40,5 +40,8 @@ cudaError_t energy_sums(const double* rho, const double* vion, const double* vh,
                         double* out8, cudaStream_t s);
 cudaError_t copy_scaled(const double2* a, double2* b, long n, double sc, cudaStream_t s);
 cudaError_t axpy(double2 a, const double2* x, double2* y, long n, cudaStream_t s);
+cudaError_t diff_to_complex(const double* a, const double* b, double2* buf, long N, cudaStream_t s);
+cudaError_t add_real(const double2* buf, double* a, long N, cudaStream_t s);
+cudaError_t kerker_factor(double* f, Grid3 g, const double* cell, double b, double q0, cudaStream_t s);
 
 }  // namespace pt

@@ -123,3 +123,14 @@ def test_ptcn_tolerance_mode_si8(pkg):
         assert abs(info_g["energy"] - info_o.energy) < 1e-8 * abs(info_o.energy)
         assert rel(s.orbitals().T, st.Psi) < 1e-7
     s.close()
+
+
+@pytest.mark.parametrize("name,n_orb", [("si64", 9), ("si216", 6)])
+def test_exchange_mixed_large_grids(pkg, name, n_orb):
+    """FP32 pair pipeline (cubic 64^3 / 96^3 kernels) on the workloads' cells with a few orbitals."""
+    w = syn.si_workload(name, relax_iters=0, n_orb=n_orb, precision="mixed")
+    model, C0 = make(w)
+    st = model.init_state(C0)
+    s = pkg.System(w, C0)
+    assert rel(s.exchange().cpu().numpy().T, st.W) < 2e-5
+    s.close()
