@@ -60,6 +60,7 @@ struct pt_system {
   float* khat32 = nullptr;
   double *hfac = nullptr, *kfac = nullptr, *rho_mix = nullptr, *vion = nullptr, *vloc = nullptr, *vh = nullptr, *rho = nullptr, *rho2 = nullptr;
   double* d_atoms = nullptr;
+  float* vloc32 = nullptr;
   double2 *psi = nullptr, *psi_half = nullptr, *psi_f = nullptr, *hpsi = nullptr, *tmp = nullptr, *rbuf = nullptr;
   double2 *wg = nullptr, *xi = nullptr, *xprev = nullptr, *rprev = nullptr, *dX = nullptr, *dR = nullptr;
   double2* hbuf = nullptr;
@@ -191,6 +192,7 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   t->rho_mix = c.take<double>(N);
   t->vion = c.take<double>(N);
   t->vloc = c.take<double>(N);
+  if (mixed) t->vloc32 = c.take<float>(N);
   t->vh = c.take<double>(N);
   t->rho = c.take<double>(N);
   t->rho2 = c.take<double>(N);
@@ -404,6 +406,49 @@ static pt_status gemm(pt_system* sys, int opA, int opB, int M, int N, int K, dou
 
 static const double2 kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMinusOne = {-1.0, 0.0};
 
+// SCF-iteration forms. In mixed precision the real-space orbitals, the
+// density they give and the local-potential product run in FP32; in FP64
+// mode these are the FP64 routines above.
+static pt_status real_orbitals_scf(pt_system* sys, const double2* c) {
+  if (!sys->mixed) return real_orbitals(sys, c);
+  return to_real<float>(sys, c, sys->ne, sys->psi_r32);
+}
+
+static pt_status density_scf(pt_system* sys, double* rho) {
+  if (sys->mixed) PT_CK(pt::density32(sys->psi_r32, sys->N, sys->ne, rho, sys->s));
+  else PT_CK(pt::density(sys->psi_r, sys->N, sys->ne, rho, sys->s));
+  return PT_OK;
+}
+
+static pt_status apply_local_scf(pt_system* sys, const double2* c, double2* out) {
+  if (!sys->mixed) return apply_local_from_real(sys, c, out);
+  PT_CK(pt::to_float(sys->vloc, sys->vloc32, sys->N, sys->s));
+  float2* hb = reinterpret_cast<float2*>(sys->hbuf);
+  for (int c0 = 0; c0 < sys->ne; c0 += sys->hb) {
+    const int cnt = std::min(sys->hb, sys->ne - c0);
+    PT_CK(pt::fft_rows<float>(sys->psi_r32 + (long)c0 * sys->N, hb, cnt, sys->g, 0, 1.0, sys->vloc32, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<float>(hb, cnt, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::fft_cols<float>(hb, cnt, sys->g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+    PT_CK(pt::gather_basis<float>(hb, out + (long)c0 * sys->npw, sys->npw, cnt, sys->g, sys->basis, sys->npw,
+                                  std::sqrt(sys->vol) / sys->N, sys->kin, c + (long)c0 * sys->npw, sys->npw, 0,
+                                  sys->s));
+  }
+  return PT_OK;
+}
+
+// S = A^H B and C -= A S (the PT projection, Alg. 3): FP32 in mixed precision
+static pt_status projection(pt_system* sys, const double2* A, double2* HB) {
+  const int ne = sys->ne, npw = sys->npw;
+  if (sys->mixed) {
+    PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, A, npw, HB, npw, kZero, sys->S, ne));
+    PT_TRY(gemm<float>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, A, npw, sys->S, ne, kOne, HB, npw));
+  } else {
+    PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, A, npw, HB, npw, kZero, sys->S, ne));
+    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, A, npw, sys->S, ne, kOne, HB, npw));
+  }
+  return PT_OK;
+}
+
 static pt_status read_status(pt_system* sys, int* h) {
   PT_CK(cudaMemcpyAsync(h, sys->status, sizeof(int), cudaMemcpyDeviceToHost, sys->s));
   PT_CK(cudaStreamSynchronize(sys->s));
@@ -520,17 +565,16 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
   const long stride = n;
   if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
   // initial residual R_n = H_n Psi_n - Psi_n (Psi_n^H H_n Psi_n) and the half step
-  PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho, sys->s));
+  PT_TRY(density_scf(sys, sys->rho));
   PT_TRY(local_potential(sys));
-  PT_TRY(apply_local_from_real(sys, sys->psi, sys->hpsi));
+  PT_TRY(apply_local_scf(sys, sys->psi, sys->hpsi));
   PT_CK(pt::axpy(kOne, sys->wg, sys->hpsi, n, sys->s));
-  PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->psi, npw, sys->hpsi, npw, kZero, sys->S, ne));
-  PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->psi, npw, sys->S, ne, kOne, sys->hpsi, npw));
+  PT_TRY(projection(sys, sys->psi, sys->hpsi));
   PT_CK(pt::half_step(sys->psi, sys->hpsi, hdt, sys->psi_half, n, sys->s));
   PT_CK(cudaMemcpyAsync(sys->psi_f, sys->psi_half, sizeof(double2) * n, cudaMemcpyDeviceToDevice, sys->s));
-  PT_TRY(real_orbitals(sys, sys->psi_f));
+  PT_TRY(real_orbitals_scf(sys, sys->psi_f));
   sys->psi_r_current = false;
-  PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho, sys->s));
+  PT_TRY(density_scf(sys, sys->rho));
   // SCF loop
   const int fixed = sys->p.scf_fixed_iters;
   const int niter = fixed > 0 ? fixed : sys->p.scf_max;
@@ -542,14 +586,12 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
   double drho = 0.0;
   for (it = 1; it <= niter; ++it) {
     PT_TRY(local_potential(sys));
-    PT_TRY(apply_local_from_real(sys, sys->psi_f, sys->hpsi));
+    PT_TRY(apply_local_scf(sys, sys->psi_f, sys->hpsi));
     if (sys->p.alpha != 0.0) {
       if (sys->p.fock_mode == PT_FOCK_EXACT) PT_TRY(exchange_sym(sys, sys->hpsi, 1));
       else PT_TRY(ace_apply(sys, sys->psi_f, ne, sys->hpsi));
     }
-    PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->psi_f, npw, sys->hpsi, npw, kZero, sys->S, ne));
-    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->psi_f, npw, sys->S, ne, kOne, sys->hpsi,
-                        npw));
+    PT_TRY(projection(sys, sys->psi_f, sys->hpsi));
     PT_CK(pt::pt_residual(sys->psi_f, sys->hpsi, sys->psi_half, hdt, sys->rbuf, n, sys->part, sys->red + 0, sys->s));
     // Anderson (per band)
     int newslot = -1;
@@ -577,8 +619,8 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
     PT_CK(pt::anderson_update(sys->psi_f, sys->rbuf, sys->dX, sys->dR, stride, sl, sys->gamma, std::max(m, 1), npw, n,
                               sys->p.anderson_beta, sys->s));
     // new density and its change
-    PT_TRY(real_orbitals(sys, sys->psi_f));
-    PT_CK(pt::density(sys->psi_r, sys->N, ne, sys->rho2, sys->s));
+    PT_TRY(real_orbitals_scf(sys, sys->psi_f));
+    PT_TRY(density_scf(sys, sys->rho2));
     PT_CK(pt::rho_change(sys->rho2, sys->rho, sys->N, sys->part, sys->red + 1, sys->s));
     std::swap(sys->rho, sys->rho2);
     if (fixed == 0) {

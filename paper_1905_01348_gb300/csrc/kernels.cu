@@ -60,6 +60,31 @@ cudaError_t density(const double2* psi_r, long N, int ne, double* rho, cudaStrea
   return cudaGetLastError();
 }
 
+__global__ void k_density32(const float2* __restrict__ psi_r, long N, int ne, double* __restrict__ rho) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < N; r += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < ne; ++k) {
+      const float2 v = psi_r[(long)k * N + r];
+      s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    rho[r] = 2.0 * s;
+  }
+}
+
+cudaError_t density32(const float2* psi_r, long N, int ne, double* rho, cudaStream_t s) {
+  k_density32<<<nblk(N, 256, 152L * 64), 256, 0, s>>>(psi_r, N, ne, rho); launched();
+  return cudaGetLastError();
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) b[t] = (float)a[t];
+}
+
+cudaError_t to_float(const double* a, float* b, long n, cudaStream_t s) {
+  k_to_float<<<nblk(n, 256), 256, 0, s>>>(a, b, n); launched();
+  return cudaGetLastError();
+}
+
 // ---- local potential -----------------------------------------------------------
 __global__ void k_rho_to_complex(const double* __restrict__ rho, double2* __restrict__ buf, long N) {
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < N; r += (long)gridDim.x * blockDim.x)

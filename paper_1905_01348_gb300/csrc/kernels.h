@@ -13,6 +13,8 @@ struct SlotList {
 };
 
 cudaError_t density(const double2* psi_r, long N, int ne, double* rho, cudaStream_t s);
+cudaError_t density32(const float2* psi_r, long N, int ne, double* rho, cudaStream_t s);
+cudaError_t to_float(const double* a, float* b, long n, cudaStream_t s);
 cudaError_t rho_to_complex(const double* rho, double2* buf, long N, cudaStream_t s);
 cudaError_t assemble_vloc(const double* vion, const double2* vh_c, const double* rho, long N, int use_h, double w_lda,
                           double* vh, double* vloc, cudaStream_t s);
