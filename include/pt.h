@@ -162,6 +162,26 @@ pt_status pt_get_timing(pt_system* s, double* pair_ms, int64_t* pairs, int64_t* 
  * systems); differences of two readings count the launches in between. */
 pt_status pt_launch_count(uint64_t* count);
 
+/* V_X Psi without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (a plug-in whose
+ * host application owns all device memory through its own allocator, or code
+ * that must not allocate after start-up, since an allocation can synchronise
+ * the device or fail under memory pressure). It computes what pt_exchange
+ * computes, for the orbitals d_psi given by the caller (n_orb x npw
+ * complex128, band-major, device; they define P and are the vectors V_X is
+ * applied to) into d_w (same shape, device), enqueued on `stream`, and
+ * synchronises that stream before returning. Only the p fields that define
+ * the grid, basis, kernel and precision are used.
+ * Scratch: a file-scope device array of 64 MiB that every GPU loading this
+ * library holds until the process exits. It must fit the real-space
+ * orbitals, the exchange accumulators and at least one pair tile;
+ * larger systems get PT_ERR_OOM with the sizes in pt_last_error(NULL).
+ * The first call on a device looks up the array's device address (set-up);
+ * make that first call before any stream capture. Every call reuses the same
+ * array and overwrites its contents (the accumulators are cleared by each
+ * call): calls that overlap on the GPU, from any stream or thread, race. */
+pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, void* stream);
+
 /* Release the handle (the workspace stays owned by the caller). */
 pt_status pt_destroy(pt_system* s);
 

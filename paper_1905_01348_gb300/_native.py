@@ -103,6 +103,7 @@ def load() -> C.CDLL:
         "pt_set_timing": (C.c_int, [vp, C.c_int]),
         "pt_get_timing": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]),
         "pt_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
+        "pt_exchange_static": (C.c_int, [P, vp, vp, vp]),
         "pt_destroy": (C.c_int, [vp]),
         "pt_last_error": (C.c_char_p, [vp]),
     }
@@ -246,6 +247,11 @@ def pt_get_timing(h, reset: bool = False) -> tuple[float, int, int]:
     groups = C.c_int64(0)
     _check(load().pt_get_timing(h, C.byref(ms), C.byref(pairs), C.byref(groups), int(bool(reset))), h)
     return ms.value, pairs.value, groups.value
+
+
+def pt_exchange_static(params: PtParams, d_psi: int, d_w: int, stream: int = 0) -> None:
+    """V_X Psi with no device allocation (scratch in a static 64 MiB device array)."""
+    _check(load().pt_exchange_static(C.byref(params), C.c_void_p(d_psi), C.c_void_p(d_w), C.c_void_p(stream)))
 
 
 def pt_launch_count() -> int:

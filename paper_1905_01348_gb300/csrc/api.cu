@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <mutex>
 
 #include "pt.h"
 #include "common.cuh"
@@ -651,6 +652,119 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
 }
 
 // ---------------------------------------------------------------------------
+// Exchange without device allocation (pt_exchange_static).
+//
+// Some callers cannot call cudaMalloc: a plug-in whose host application owns
+// all device memory through its own allocator, or code that must not
+// allocate after its start-up phase (an allocation can synchronise the
+// device or fail under memory pressure). pt_exchange_static serves them: it
+// keeps every buffer it needs in the file-scope array below, which exists on
+// every GPU that loads this library until the process exits.
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static void* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress (with that device current).
+static pt_status static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { g_last_error = "pt_exchange_static: cudaGetDevice -> " + pt::cuda_msg(e); return PT_ERR_CUDA; }
+  if (dev < 0 || dev >= kMaxDevices) { g_last_error = "pt_exchange_static: device index out of range"; return PT_ERR_INVALID; }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_addr[dev] == nullptr) {
+    void* addr = nullptr;
+    e = cudaGetSymbolAddress(&addr, g_static_scratch);
+    if (e != cudaSuccess || addr == nullptr) {
+      g_last_error = "pt_exchange_static: cudaGetSymbolAddress -> " + pt::cuda_msg(e);
+      return PT_ERR_CUDA;
+    }
+    g_static_addr[dev] = addr;
+  }
+  *out = g_static_addr[dev];
+  return PT_OK;
+}
+
+// Layout of the static scratch for one call; returns the bytes needed (base 0 sizes it).
+static size_t static_layout(pt_system* t, const pt_params* p, int npw, uintptr_t base, int tpl) {
+  Carver c{base};
+  const long N = (long)p->n[0] * p->n[1] * p->n[2];
+  const long ne = p->n_orb;
+  const bool mixed = p->precision == PT_MIXED;
+  const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
+  const int tile = choose_tile(p);
+  const long nb = (ne + tile - 1) / tile;
+  t->basis = c.take<int>(npw);
+  t->tw64 = c.take<double2>(pt::kTwiddleTotal);
+  t->tw32 = c.take<float2>(pt::kTwiddleTotal);
+  if (mixed) t->khat32 = c.take<float>(N); else t->khat64 = c.take<double>(N);
+  t->psi_r = c.take<double2>((size_t)N * ne);
+  if (mixed) t->psi_r32 = c.take<float2>((size_t)N * ne);
+  t->w_r = c.take<unsigned char>((size_t)N * ne * cs);
+  t->d_tiles_sym = c.take<pt::PairTile>((size_t)(nb * (nb - 1) / 2 + nb));
+  t->scratch = c.take<unsigned char>((size_t)tpl * pt::kTileMax * pt::kTileMax * N * cs);
+  return c.off + 256;
+}
+
+static pt_status exchange_static_body(pt_system* t, const pt_params* p, const std::vector<int>& idx,
+                                      const double2* d_psi, double2* d_w) {
+  pt_system* sys = t;   // for PT_CK messages
+  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+  std::vector<double2> tw(pt::kTwiddleTotal);
+  pt::twiddle_host(tw.data());
+  std::vector<float2> tw32(pt::kTwiddleTotal);
+  for (int k = 0; k < pt::kTwiddleTotal; ++k) tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+  const double w2 = p->omega * p->omega;
+  std::vector<double> kt((size_t)t->N);
+  for (int i2 = 0; i2 < n2; ++i2)
+    for (int i0 = 0; i0 < n0; ++i0)
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const double g0 = 2.0 * M_PI * freq(i0, n0) / p->cell[0];
+        const double g1 = 2.0 * M_PI * freq(i1, n1) / p->cell[1];
+        const double gz = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
+        const double gg = g0 * g0 + g1 * g1 + gz * gz;
+        const double k = gg > 0.0 ? 4.0 * M_PI * (-std::expm1(-gg / (4.0 * w2))) / gg : M_PI / w2;
+        kt[((size_t)i2 * n0 + i0) * n1 + i1] = -p->alpha * k / (double)t->N;
+      }
+  cudaStream_t s = t->s;
+  PT_CK(cudaMemcpyAsync(t->basis, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(t->tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(t->tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice, s));
+  if (t->mixed) {
+    std::vector<float> kf(kt.size());
+    for (size_t k = 0; k < kt.size(); ++k) kf[k] = (float)kt[k];
+    PT_CK(cudaMemcpyAsync(t->khat32, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaStreamSynchronize(s));
+  } else {
+    PT_CK(cudaMemcpyAsync(t->khat64, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice, s));
+  }
+  pt::PairTile* tiles = nullptr;
+  int *lf = nullptr, *lc = nullptr, nl = 0;
+  const int nt = pt::fock_build_tiles(t->ne, 0, t->plan_sym.tile, 1, t->plan_sym.tiles_per_launch, &tiles, &lf, &lc, &nl);
+  if (nt < 0) { t->err = "pt_exchange_static: tile schedule"; return PT_ERR_INVALID; }
+  t->plan_sym.n_launch = nl;
+  t->plan_sym.launch_first = lf;
+  t->plan_sym.launch_count = lc;
+  t->plan_sym.n_tiles = nt;
+  t->plan_sym.d_tiles = t->d_tiles_sym;
+  cudaError_t e = cudaMemcpyAsync(t->d_tiles_sym, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  std::free(tiles);
+  if (e != cudaSuccess) { t->err = "pt_exchange_static: tile upload -> " + pt::cuda_msg(e); return PT_ERR_CUDA; }
+  t->tw.d64 = t->tw64;
+  t->tw.d32 = t->tw32;
+  // real-space orbitals, then the pair pipeline (it zeroes the accumulators itself)
+  PT_TRY(real_orbitals(t, d_psi));
+  PT_TRY(exchange_sym(t, d_w, 0));
+  PT_CK(cudaStreamSynchronize(s));
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 
 extern "C" {
@@ -933,6 +1047,54 @@ pt_status pt_get_timing(pt_system* sys, double* pair_ms, int64_t* pairs, int64_t
   if (launch_groups) *launch_groups = sys->t_groups;
   if (reset) { sys->t_pair_ms = 0.0; sys->t_pairs = 0; sys->t_groups = 0; }
   return PT_OK;
+}
+
+pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, void* stream) {
+  std::string why;
+  pt_status st = check_params(p, &why);
+  if (st != PT_OK) { g_last_error = "pt_exchange_static: " + why; return st; }
+  if (d_psi == nullptr || d_w == nullptr) { g_last_error = "pt_exchange_static: NULL orbitals or output"; return PT_ERR_INVALID; }
+  std::vector<int> idx;
+  basis_list(p, &idx, nullptr);
+  const long N = (long)p->n[0] * p->n[1] * p->n[2];
+  const size_t cs = p->precision == PT_MIXED ? sizeof(float2) : sizeof(double2);
+  const int tile = choose_tile(p);
+  const int nb = (p->n_orb + tile - 1) / tile;
+  pt_system probe;
+  const size_t fixed = static_layout(&probe, p, (int)idx.size(), 0, 0);
+  const size_t per_tile = (size_t)pt::kTileMax * pt::kTileMax * N * cs;
+  if (fixed + per_tile > kStaticScratchBytes) {
+    g_last_error = "pt_exchange_static: this system needs " + std::to_string(fixed + per_tile) +
+                   " bytes of scratch (orbitals, accumulators, one pair tile); the static array holds " +
+                   std::to_string(kStaticScratchBytes) + " bytes. Use pt_exchange with a workspace.";
+    return PT_ERR_OOM;
+  }
+  const int tpl = (int)std::min<size_t>((size_t)nb, (kStaticScratchBytes - fixed) / per_tile);
+  void* base = nullptr;
+  st = static_scratch_address(&base);
+  if (st != PT_OK) return st;
+  pt_system t;
+  t.p = *p;
+  t.p.atom_frac = nullptr;
+  t.s = (cudaStream_t)stream;
+  t.g = Grid3{p->n[0], p->n[1], p->n[2]};
+  t.N = N;
+  t.npw = (int)idx.size();
+  t.ne = p->n_orb;
+  t.hb = h_batch(p);
+  t.vol = p->cell[0] * p->cell[1] * p->cell[2];
+  t.dV = t.vol / (double)N;
+  t.mixed = p->precision == PT_MIXED;
+  t.plan_sym.tile = tile;
+  t.plan_sym.tiles_per_launch = tpl;
+  static_layout(&t, p, t.npw, (uintptr_t)base, tpl);
+  st = exchange_static_body(&t, p, idx, (const double2*)d_psi, (double2*)d_w);
+  std::free(t.plan_sym.launch_first);
+  std::free(t.plan_sym.launch_count);
+  t.plan_sym.launch_first = nullptr;
+  t.plan_sym.launch_count = nullptr;
+  if (st != PT_OK) g_last_error = t.err;
+  return st;
 }
 
 pt_status pt_launch_count(uint64_t* count) {
