@@ -329,6 +329,18 @@ static pt_status apply_local(pt_system* sys, const double2* X, double2* out, int
 }
 
 // V_X Psi for the orbitals whose real-space form is in psi_r; out = (or +=) result
+// A bounded device wait in the pair kernels that gave up leaves 1 in the flag.
+static pt_status check_pair_flag(pt_system* sys) {
+  int h = 0;
+  PT_CK(cudaMemcpyAsync(&h, sys->plan_sym.d_err, sizeof(int), cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  if (h != 0) {
+    sys->err = "exchange: a pair kernel timed out waiting for a bulk copy";
+    return PT_ERR_TIMEOUT;
+  }
+  return PT_OK;
+}
+
 template <typename T>
 static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
   const size_t cs = sizeof(pt::cplx<T>);
@@ -346,6 +358,7 @@ static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
     sys->t_pairs += (long long)sys->ne * (sys->ne + 1) / 2;
     sys->t_groups += sys->plan_sym.n_launch;
   }
+  PT_TRY(check_pair_flag(sys));
   return to_basis<T>(sys, sys->w_r, sys->ne, out, accumulate, nullptr, nullptr);
 }
 
@@ -381,6 +394,7 @@ static pt_status ensure_plan_x(pt_system* sys, int ncols) {
   sys->plan_x.launch_count = lc;
   sys->plan_x.d_tiles = sys->d_tiles_x;
   sys->plan_x.n_tiles = nt;
+  sys->plan_x.d_err = sys->status + 4;
   sys->plan_x_ncols = ncols;
   return PT_OK;
 }
@@ -394,6 +408,7 @@ static pt_status exchange_x_t(pt_system* sys, const double2* X, int ncols, doubl
   const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
   const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
   PT_CK(pt::fock_pairs<T>(pr, sys->x_r, nullptr, sys->w_r, sys->plan_x, 0, sys->g, kt, sys->scratch, sys->tw, sys->s));
+  PT_TRY(check_pair_flag(sys));
   return to_basis<T>(sys, sys->w_r, ncols, out, 1, nullptr, nullptr);
 }
 
@@ -706,6 +721,7 @@ static size_t static_layout(pt_system* t, const pt_params* p, int npw, uintptr_t
   if (mixed) t->psi_r32 = c.take<float2>((size_t)N * ne);
   t->w_r = c.take<unsigned char>((size_t)N * ne * cs);
   t->d_tiles_sym = c.take<pt::PairTile>((size_t)(nb * (nb - 1) / 2 + nb));
+  t->status = c.take<int>(16);
   t->scratch = c.take<unsigned char>((size_t)tpl * pt::kTileMax * pt::kTileMax * N * cs);
   return c.off + 256;
 }
@@ -751,6 +767,8 @@ static pt_status exchange_static_body(pt_system* t, const pt_params* p, const st
   t->plan_sym.launch_count = lc;
   t->plan_sym.n_tiles = nt;
   t->plan_sym.d_tiles = t->d_tiles_sym;
+  t->plan_sym.d_err = t->status + 4;
+  PT_CK(cudaMemsetAsync(t->status, 0, sizeof(int) * 16, s));
   cudaError_t e = cudaMemcpyAsync(t->d_tiles_sym, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   std::free(tiles);
@@ -871,7 +889,9 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
     sys->plan_sym.launch_count = lc;
     sys->plan_sym.d_tiles = sys->d_tiles_sym;
     sys->plan_sym.n_tiles = nt;
+    sys->plan_sym.d_err = sys->status + 4;
   }
+  PT_CK(cudaMemsetAsync(sys->status, 0, sizeof(int) * 16, s));
   PT_CK(cudaStreamSynchronize(s));
   // device tables
   PT_CK(pt::hartree_factor(sys->hfac, sys->g, p->cell, s));

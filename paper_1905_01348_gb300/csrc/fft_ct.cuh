@@ -54,28 +54,34 @@ template <> struct Plan2<32> { static constexpr int R1 = 8, R2 = 4; };
 template <> struct Plan2<64> { static constexpr int R1 = 8, R2 = 8; };
 template <> struct Plan2<96> { static constexpr int R1 = 8, R2 = 12; };
 
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
-constexpr int padded(int n) { return n + n / 8 + 1; }
+// Line buffers in shared memory are laid out with a row stride of L + 1
+// complex values (rows = lines of the row-wise transforms), and every stage
+// maps consecutive threads to consecutive lines with the same butterfly
+// index. A half-warp then touches 16 different rows whose addresses differ by
+// L + 1 = 1 (mod 16) complex values: the 64-bit accesses of a half-warp fall
+// on 16 distinct bank pairs for row- and column-wise stages alike, and the
+// twiddle index is uniform across the warp (a shared-memory broadcast).
 
-// One Stockham stage over lines of length L. Element e of line l is
-// buf[pidx(l * LSTR + e * ESTR)]. LM: consecutive threads walk along a line
-// (line count nl may be below NL); otherwise across lines (nl == NL).
-template <typename C, bool INV, int L, int R, int NS, int NL, int NT, bool LM, int LSTR, int ESTR>
-__device__ __forceinline__ void ct_stage(C* buf, int nl, const C* __restrict__ tw, int tid) {
+// One Stockham stage over lines [line0, line0 + nl) of length L. Element e of
+// line l of `src` is src[l * SLS + e * SES]; the output goes to `dst` with
+// strides (DLS, DES). src == dst gives the in-place form (all reads of the
+// stage finish before the first write). Lines at or beyond nl are skipped
+// (NL is the compile-time line capacity of one call).
+template <typename C, bool INV, int L, int R, int NS, int NL, int NT, int SLS, int SES, int DLS, int DES>
+__device__ __forceinline__ void ct_stage_io(const C* src, C* dst, int nl, const C* __restrict__ tw, int tid,
+                                            int line0 = 0) {
   constexpr int NBL = L / R;
   constexpr int MB = (NL * NBL + NT - 1) / NT;
   constexpr int TWS = L / (NS * R);
-  const int total = nl * NBL;
   C v[MB][R];
 #pragma unroll
   for (int q = 0; q < MB; ++q) {
     const int b = tid + q * NT;
-    if (b < total) {
-      const int line = LM ? b / NBL : b % NL;
-      const int j = LM ? b % NBL : b / NL;
-      const int base = line * LSTR;
+    const int ll = b % NL, j = b / NL;
+    if (j < NBL && ll < nl) {
+      const int base = (line0 + ll) * SLS;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = buf[pidx(base + (j + r * NBL) * ESTR)];
+      for (int r = 0; r < R; ++r) v[q][r] = src[base + (j + r * NBL) * SES];
       if (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -92,37 +98,40 @@ __device__ __forceinline__ void ct_stage(C* buf, int nl, const C* __restrict__ t
 #pragma unroll
   for (int q = 0; q < MB; ++q) {
     const int b = tid + q * NT;
-    if (b < total) {
-      const int line = LM ? b / NBL : b % NL;
-      const int j = LM ? b % NBL : b / NL;
-      const int base = line * LSTR;
+    const int ll = b % NL, j = b / NL;
+    if (j < NBL && ll < nl) {
+      const int base = (line0 + ll) * DLS;
       const int k = j % NS;
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pidx(base + (o + r * NS) * ESTR)] = v[q][r];
+      for (int r = 0; r < R; ++r) dst[base + (o + r * NS) * DES] = v[q][r];
     }
   }
   __syncthreads();
 }
 
+template <typename C, bool INV, int L, int R, int NS, int NL, int NT, int LS, int ES>
+__device__ __forceinline__ void ct_stage(C* buf, int nl, const C* __restrict__ tw, int tid, int line0 = 0) {
+  ct_stage_io<C, INV, L, R, NS, NL, NT, LS, ES, LS, ES>(buf, buf, nl, tw, tid, line0);
+}
+
 // Forward stage 2 of plan (R1, R2), multiply each element by mul(line, e),
 // inverse stage 1 of plan (R2, R1); all in registers between one read and one write.
-template <typename C, int L, int NL, int NT, bool LM, int LSTR, int ESTR, class Mul>
-__device__ __forceinline__ void ct_fused(C* buf, int nl, const C* __restrict__ tw, int tid, Mul mul) {
+template <typename C, int L, int NL, int NT, int LS, int ES, class Mul>
+__device__ __forceinline__ void ct_fused(C* buf, int nl, const C* __restrict__ tw, int tid, Mul mul, int line0 = 0) {
   constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
   constexpr int NBL = R1;   // = L / R2
   constexpr int MB = (NL * NBL + NT - 1) / NT;
-  const int total = nl * NBL;
   C v[MB][R2];
 #pragma unroll
   for (int q = 0; q < MB; ++q) {
     const int b = tid + q * NT;
-    if (b < total) {
-      const int line = LM ? b / NBL : b % NL;
-      const int j = LM ? b % NBL : b / NL;
-      const int base = line * LSTR;
+    const int ll = b % NL, j = b / NL;
+    if (j < NBL && ll < nl) {
+      const int line = line0 + ll;
+      const int base = line * LS;
 #pragma unroll
-      for (int r = 0; r < R2; ++r) v[q][r] = buf[pidx(base + (j + r * R1) * ESTR)];
+      for (int r = 0; r < R2; ++r) v[q][r] = buf[base + (j + r * R1) * ES];
 #pragma unroll
       for (int r = 1; r < R2; ++r) v[q][r] = cmul(v[q][r], tw[r * j]);
       dftc<R2, false>(v[q]);
@@ -135,43 +144,71 @@ __device__ __forceinline__ void ct_fused(C* buf, int nl, const C* __restrict__ t
 #pragma unroll
   for (int q = 0; q < MB; ++q) {
     const int b = tid + q * NT;
-    if (b < total) {
-      const int line = LM ? b / NBL : b % NL;
-      const int j = LM ? b % NBL : b / NL;
-      const int base = line * LSTR;
+    const int ll = b % NL, j = b / NL;
+    if (j < NBL && ll < nl) {
+      const int base = (line0 + ll) * LS;
 #pragma unroll
-      for (int r = 0; r < R2; ++r) buf[pidx(base + (j * R2 + r) * ESTR)] = v[q][r];
+      for (int r = 0; r < R2; ++r) buf[base + (j * R2 + r) * ES] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-// Full forward (plan R1, R2) and inverse (plan R2, R1) line transforms.
-template <typename C, int L, int NL, int NT, bool LM, int LSTR, int ESTR>
-__device__ __forceinline__ void ct_forward(C* buf, int nl, const C* tw, int tid) {
-  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
-  ct_stage<C, false, L, R1, 1, NL, NT, LM, LSTR, ESTR>(buf, nl, tw, tid);
-  ct_stage<C, false, L, R2, R1, NL, NT, LM, LSTR, ESTR>(buf, nl, tw, tid);
+// ---- bulk copies (TMA, non-tensor) and mbarriers --------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-template <typename C, int L, int NL, int NT, bool LM, int LSTR, int ESTR>
-__device__ __forceinline__ void ct_inverse(C* buf, int nl, const C* tw, int tid) {
-  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
-  ct_stage<C, true, L, R2, 1, NL, NT, LM, LSTR, ESTR>(buf, nl, tw, tid);
-  ct_stage<C, true, L, R1, R2, NL, NT, LM, LSTR, ESTR>(buf, nl, tw, tid);
+// one arrival that also announces `bytes` of incoming transaction
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
 
-// inverse stage 2 alone (after ct_fused)
-template <typename C, int L, int NL, int NT, bool LM, int LSTR, int ESTR>
-__device__ __forceinline__ void ct_inverse_stage2(C* buf, int nl, const C* tw, int tid) {
-  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
-  ct_stage<C, true, L, R1, R2, NL, NT, LM, LSTR, ESTR>(buf, nl, tw, tid);
+// global -> shared bulk copy completing on `bar`; addresses 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
-template <typename C, int L, int NL, int NT, bool LM, int LSTR, int ESTR>
-__device__ __forceinline__ void ct_forward_stage1(C* buf, int nl, const C* tw, int tid) {
-  constexpr int R1 = Plan2<L>::R1;
-  ct_stage<C, false, L, R1, 1, NL, NT, LM, LSTR, ESTR>(buf, nl, tw, tid);
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok)
+               : "r"(smem_u32(bar)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` with an iteration cap; false when the cap is hit.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// order earlier generic-proxy accesses of shared memory before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Full forward (plan R1, R2) and inverse (plan R2, R1) line transforms in place.
+template <typename C, int L, int NL, int NT, int LS, int ES>
+__device__ __forceinline__ void ct_forward(C* buf, int nl, const C* tw, int tid, int line0 = 0) {
+  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
+  ct_stage<C, false, L, R1, 1, NL, NT, LS, ES>(buf, nl, tw, tid, line0);
+  ct_stage<C, false, L, R2, R1, NL, NT, LS, ES>(buf, nl, tw, tid, line0);
+}
+
+template <typename C, int L, int NL, int NT, int LS, int ES>
+__device__ __forceinline__ void ct_inverse(C* buf, int nl, const C* tw, int tid, int line0 = 0) {
+  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
+  ct_stage<C, true, L, R2, 1, NL, NT, LS, ES>(buf, nl, tw, tid, line0);
+  ct_stage<C, true, L, R1, R2, NL, NT, LS, ES>(buf, nl, tw, tid, line0);
 }
 
 }  // namespace pt

@@ -18,20 +18,38 @@ constexpr int TT = kTileMax;   // orbitals per tile edge
 constexpr int RR = 4;          // grid rows per block in F1 / F3
 constexpr int NPAIR = TT * TT;
 
+// NT2 threads transform SUB lines of a slab per stage call (L / SUB calls per stage).
 template <int L> struct Cfg;
-template <> struct Cfg<32> { static constexpr int NT13 = 256, NT2 = 128, MIN2 = 4; };
-template <> struct Cfg<64> { static constexpr int NT13 = 256, NT2 = 512, MIN2 = 1; };
-template <> struct Cfg<96> { static constexpr int NT13 = 256, NT2 = 768, MIN2 = 1; };
+template <> struct Cfg<32> { static constexpr int NT13 = 256, NT2 = 128, SUB = 32; };
+template <> struct Cfg<64> { static constexpr int NT13 = 256, NT2 = 512, SUB = 64; };
+template <> struct Cfg<96> { static constexpr int NT13 = 256, NT2 = 576, SUB = 48; };
 
-template <int L> constexpr size_t smem13() {
-  return sizeof(float2) * (size_t)(L + 2 * TT * RR * L + padded(NPAIR * RR * L));
+template <int L> constexpr int WS = L + 1;   // work-buffer row stride (complex values)
+template <int L> constexpr int LS = L + 2;   // landing-buffer row stride (16-byte multiple)
+
+template <int L> constexpr size_t smem13() { return sizeof(float2) * (size_t)(L + NPAIR * RR * WS<L>); }
+template <int L> constexpr size_t smem2() { return sizeof(float2) * (size_t)(L * LS<L> + L + L * WS<L>); }
+
+__device__ __forceinline__ const float2* orb_ptr(const PairTile& tl, int o, const float2* psi_r, const float2* x_r,
+                                                 long N) {
+  return (tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N;
 }
-template <int L> constexpr size_t smem2() { return sizeof(float2) * (size_t)(L + padded(L * L)); }
+
+// Warp 0 brings one (i0, i1) slab into the landing buffer, one bulk copy per row.
+template <int L>
+__device__ __forceinline__ void issue_slab(float2* land, const float2* slab, unsigned long long* bar) {
+  constexpr uint32_t ROWB = L * sizeof(float2);
+  const int lane = threadIdx.x;
+  if (lane == 0) mbar_expect_tx(bar, ROWB * L);
+  __syncwarp();
+  for (int row = lane; row < L; row += 32) bulk_load(land + row * LS<L>, slab + (long)row * L, ROWB, bar);
+}
 
 }  // namespace
 
-// F1: pair products of RR grid rows for every pair of the tile, forward FFT
-// along axis 2, store X[slot][i2][i0][i1].
+// F1: pair products of RR grid rows for every pair of the tile (orbital rows
+// read through the read-only cache), forward FFT along axis 2, store
+// X[slot][i2][i0][i1].
 template <int L>
 __global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f1(const float2* __restrict__ psi_r,
                                                           const float2* __restrict__ x_r,
@@ -40,11 +58,10 @@ __global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f1(const float2* __restri
   constexpr int NT = Cfg<L>::NT13;
   constexpr int ROW = RR * L;
   constexpr long N = (long)L * L * L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ PairTile tl;
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* orb = tw + L;
-  float2* work = orb + 2 * TT * ROW;
+  float2* work = tw + L;
   const int tid = threadIdx.x;
   if (tid == 0) tl = tiles[tile0 + blockIdx.y];
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
@@ -53,54 +70,111 @@ __global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f1(const float2* __restri
   const int i0 = blockIdx.x / NB1;
   const int i1s = (blockIdx.x % NB1) * RR;
   const long roff = ((long)i0 * L + i1s) * L;
-  for (int o = 0; o < tl.n_orb; ++o) {
-    const float4* src = reinterpret_cast<const float4*>((tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N + roff);
-    float4* dst = reinterpret_cast<float4*>(orb + o * ROW);
-    for (int e = tid; e < ROW / 2; e += NT) dst[e] = src[e];
-  }
-  __syncthreads();
   const int np = tl.n_pairs;
   for (int idx = tid; idx < np * ROW; idx += NT) {
     const int p = idx / ROW, e = idx % ROW;
-    work[pidx(idx)] = cmulc(orb[tl.pi[p] * ROW + e], orb[tl.pj[p] * ROW + e]);
+    const float2 a = __ldg(orb_ptr(tl, tl.pi[p], psi_r, x_r, N) + roff + e);
+    const float2 b = __ldg(orb_ptr(tl, tl.pj[p], psi_r, x_r, N) + roff + e);
+    work[(p * RR + e / L) * WS<L> + e % L] = cmulc(a, b);
   }
   __syncthreads();
-  ct_forward<float2, L, NPAIR * RR, NT, true, L, 1>(work, np * RR, tw, tid);
+  ct_forward<float2, L, NPAIR * RR, NT, WS<L>, 1>(work, np * RR, tw, tid);
   const long slot0 = (long)blockIdx.y * NPAIR;
   for (int idx = tid; idx < np * ROW; idx += NT) {
     const int r = idx % RR;
     const int rest = idx / RR;
     const int i2 = rest % L;
     const int p = rest / L;
-    X[(((slot0 + p) * L + i2) * L + i0) * L + i1s + r] = work[pidx((p * RR + r) * L + i2)];
+    X[(((slot0 + p) * L + i2) * L + i0) * L + i1s + r] = work[(p * RR + r) * WS<L> + i2];
   }
 }
 
-// F2: one (pair, i2) slab: FFT along axis 1 and axis 0, multiply by the
-// screened kernel, inverse along axis 0 and axis 1.
+// F2: persistent blocks walk the (pair slot, i2) slabs of the launch. The
+// next slab is brought into the landing buffer by bulk copies (TMA) as soon
+// as the current one has been read out of it, so the load overlaps the
+// transforms: FFT along axis 1 and axis 0, multiply by the screened kernel,
+// inverse along axis 0 and axis 1. A wait that exceeds its iteration cap sets
+// *err and ends the block after a second bounded wait for its copy in flight.
 template <int L>
-__global__ void __launch_bounds__(Cfg<L>::NT2, Cfg<L>::MIN2) k_fast_f2(float2* __restrict__ X, const PairTile* __restrict__ tiles,
-                                                         int tile0, const float* __restrict__ khat_t,
-                                                         const float2* __restrict__ tw_g) {
+__global__ void __launch_bounds__(Cfg<L>::NT2, 1) k_fast_f2(float2* __restrict__ X, const PairTile* __restrict__ tiles,
+                                                            int tile0, int nslot, const float* __restrict__ khat_t,
+                                                            const float2* __restrict__ tw_g, int* __restrict__ err) {
   constexpr int NT = Cfg<L>::NT2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x;
-  const int slot = blockIdx.y;
-  if (slot % NPAIR >= tiles[tile0 + slot / NPAIR].n_pairs) return;
-  const int i2 = blockIdx.x;
-  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  constexpr int SUB = Cfg<L>::SUB;
+  constexpr int SLAB = L * L;
+  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
+  constexpr int W = WS<L>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int s_abort;
+  float2* land = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = land + L * LS<L>;
   float2* buf = tw + L;
+  const int tid = threadIdx.x;
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
-  float2* slab = X + ((long)slot * L + i2) * (L * L);
-  for (int e = tid; e < L * L; e += NT) buf[pidx(e)] = slab[e];
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+  }
   __syncthreads();
-  ct_forward<float2, L, L, NT, true, L, 1>(buf, L, tw, tid);          // axis 1 (rows)
-  ct_forward_stage1<float2, L, L, NT, false, 1, L>(buf, L, tw, tid);  // axis 0 (columns)
-  const float* kt = khat_t + (long)i2 * (L * L);
-  ct_fused<float2, L, L, NT, false, 1, L>(buf, L, tw, tid, [kt](int line, int e) { return kt[e * L + line]; });
-  ct_inverse_stage2<float2, L, L, NT, false, 1, L>(buf, L, tw, tid);
-  ct_inverse<float2, L, L, NT, true, L, 1>(buf, L, tw, tid);
-  for (int e = tid; e < L * L; e += NT) slab[e] = buf[pidx(e)];
+  const long total = (long)nslot * L;
+  auto active = [&](long sl) {
+    const int slot = (int)(sl / L);
+    return (slot % NPAIR) < tiles[tile0 + slot / NPAIR].n_pairs;
+  };
+  long s = blockIdx.x;
+  while (s < total && !active(s)) s += gridDim.x;
+  uint32_t phase = 0;
+  bool in_flight = s < total;
+  if (tid < 32 && s < total) issue_slab<L>(land, X + s * SLAB, &bar);
+  while (s < total) {
+    long nxt = s + gridDim.x;
+    while (nxt < total && !active(nxt)) nxt += gridDim.x;
+    if (!mbar_wait_bounded(&bar, phase)) atomicExch(&s_abort, 1);
+    __syncthreads();
+    if (s_abort) break;
+    phase ^= 1u;
+    in_flight = false;
+    const int i2 = (int)(s % L);
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)   // axis 1 (rows), stage 1: landing buffer -> work buffer
+      ct_stage_io<float2, false, L, R1, 1, SUB, NT, LS<L>, 1, W, 1>(land, buf, SUB, tw, tid, l0);
+    if (nxt < total) {
+      if (tid < 32) {
+        if (tid == 0) fence_proxy_async_smem();
+        __syncwarp();
+        issue_slab<L>(land, X + nxt * SLAB, &bar);
+      }
+      in_flight = true;
+    }
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)
+      ct_stage<float2, false, L, R2, R1, SUB, NT, W, 1>(buf, SUB, tw, tid, l0);     // axis 1, stage 2
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)
+      ct_stage<float2, false, L, R1, 1, SUB, NT, 1, W>(buf, SUB, tw, tid, l0);      // axis 0, stage 1
+    const float* kt = khat_t + (long)i2 * SLAB;
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)
+      ct_fused<float2, L, SUB, NT, 1, W>(buf, SUB, tw, tid,
+                                        [kt](int line, int e) { return __ldg(kt + e * L + line); }, l0);
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)
+      ct_stage<float2, true, L, R1, R2, SUB, NT, 1, W>(buf, SUB, tw, tid, l0);      // axis 0, inverse stage 2
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)
+      ct_stage<float2, true, L, R2, 1, SUB, NT, W, 1>(buf, SUB, tw, tid, l0);       // axis 1, inverse stage 1
+#pragma unroll 1
+    for (int l0 = 0; l0 < L; l0 += SUB)
+      ct_stage<float2, true, L, R1, R2, SUB, NT, W, 1>(buf, SUB, tw, tid, l0);      // axis 1, inverse stage 2
+    float2* slab = X + s * SLAB;
+    for (int e = tid; e < SLAB; e += NT) slab[e] = buf[(e / L) * W + e % L];
+    s = nxt;
+  }
+  if (s_abort) {
+    if (tid == 0) atomicExch(err, 1);
+    if (in_flight) (void)mbar_wait_bounded(&bar, phase);
+  }
 }
 
 // F3: inverse FFT along axis 2 for all pairs of the tile, then each output
@@ -114,11 +188,10 @@ __global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f3(const float2* __restri
   constexpr int NT = Cfg<L>::NT13;
   constexpr int ROW = RR * L;
   constexpr long N = (long)L * L * L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ PairTile tl;
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* orb = tw + L;
-  float2* work = orb + 2 * TT * ROW;
+  float2* work = tw + L;
   const int tid = threadIdx.x;
   if (tid == 0) tl = tiles[tile0 + blockIdx.y];
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
@@ -134,24 +207,20 @@ __global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f3(const float2* __restri
     const int rest = idx / RR;
     const int i2 = rest % L;
     const int p = rest / L;
-    work[pidx((p * RR + r) * L + i2)] = X[(((slot0 + p) * L + i2) * L + i0) * L + i1s + r];
-  }
-  for (int o = 0; o < tl.n_orb; ++o) {
-    const float4* src = reinterpret_cast<const float4*>((tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N + roff);
-    float4* dst = reinterpret_cast<float4*>(orb + o * ROW);
-    for (int e = tid; e < ROW / 2; e += NT) dst[e] = src[e];
+    work[(p * RR + r) * WS<L> + i2] = X[(((slot0 + p) * L + i2) * L + i0) * L + i1s + r];
   }
   __syncthreads();
-  ct_inverse<float2, L, NPAIR * RR, NT, true, L, 1>(work, np * RR, tw, tid);
+  ct_inverse<float2, L, NPAIR * RR, NT, WS<L>, 1>(work, np * RR, tw, tid);
   for (int o = 0; o < tl.n_orb; ++o) {
     const int n = tl.out_n[o];
     if (!tl.is_out[o] || n == 0) continue;
     float2* dst = (tl.src[o] == 0 ? w_occ : w_x) + (long)tl.orb[o] * N + roff;
     for (int e = tid; e < ROW; e += NT) {
+      const int r = e / L, i2 = e % L;
       float2 acc = make_float2(0.f, 0.f);
       for (int c = 0; c < n; ++c) {
-        const float2 v = work[pidx(tl.out_pair[o][c] * ROW + e)];
-        const float2 a = orb[tl.out_other[o][c] * ROW + e];
+        const float2 v = work[(tl.out_pair[o][c] * RR + r) * WS<L> + i2];
+        const float2 a = __ldg(orb_ptr(tl, tl.out_other[o][c], psi_r, x_r, N) + roff + e);
         acc = cadd(acc, tl.out_conj[o][c] ? cmul_conj(a, v) : cmul(a, v));
       }
       dst[e] = cadd(dst[e], acc);
@@ -162,24 +231,33 @@ __global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f3(const float2* __restri
 template <int L>
 static cudaError_t launch_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan,
                                const float* khat_t, void* scratch, const float2* tw, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static bool init = false;
+  static int grid2 = 0;
+  if (!init) {
     cudaError_t e = cudaFuncSetAttribute(k_fast_f1<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f2<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
     if (e != cudaSuccess) return e;
-    attr = true;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast_f2<L>, Cfg<L>::NT2, smem2<L>());
+    if (e != cudaSuccess) return e;
+    grid2 = sms * std::max(1, per_sm);
+    init = true;
   }
+  if (plan.d_err == nullptr) return cudaErrorInvalidValue;
   float2* X = (float2*)scratch;
   for (int l = 0; l < plan.n_launch; ++l) {
     const int t0 = plan.launch_first[l], nt = plan.launch_count[l];
     dim3 g13((unsigned)(L * (L / RR)), (unsigned)nt);
     k_fast_f1<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>((const float2*)psi_r, (const float2*)x_r, plan.d_tiles, t0, X,
                                                          tw);
-    dim3 g2((unsigned)L, (unsigned)(nt * NPAIR));
-    k_fast_f2<L><<<g2, Cfg<L>::NT2, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw);
+    k_fast_f2<L><<<grid2, Cfg<L>::NT2, smem2<L>(), s>>>(X, plan.d_tiles, t0, nt * NPAIR, khat_t, tw, plan.d_err);
     k_fast_f3<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>((const float2*)psi_r, (const float2*)x_r, (float2*)w_occ,
                                                          (float2*)w_x, plan.d_tiles, t0, X, tw);
     launched(3);

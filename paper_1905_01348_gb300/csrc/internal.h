@@ -78,6 +78,7 @@ struct FockPlan {
   int* launch_count;
   PairTile* d_tiles;      // device
   int n_tiles;
+  int* d_err;             // device flag set to 1 when a bounded wait in a pair kernel gives up
 };
 
 template <typename T>
