@@ -244,12 +244,14 @@ def run_gpu(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = pkg.pt_launch_count()
+    torch.cuda.nvtx.range_push("timed_steps")
     e0.record(stream)
     infos = []
     for _ in range(args.steps):
         st, info = sysg.step()
         infos.append(info)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = pkg.pt_launch_count() - launches0
     clk = clocks.stop()
