@@ -158,6 +158,14 @@ pt_status pt_orbitals_device(pt_system* s, void** d_psi);
 pt_status pt_set_timing(pt_system* s, int enable);
 pt_status pt_get_timing(pt_system* s, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset);
 
+/* Failure-detection self-test (no counterpart in the paper). Launches one
+ * block that waits, with a small iteration cap, on an mbarrier transfer that
+ * is never issued, exactly as the pair kernels wait for their bulk copies.
+ * The wait gives up, the kernel writes 1 to the caller's device int d_flag,
+ * and the call returns PT_ERR_TIMEOUT with the context still usable. Any
+ * other status means the bounded-wait path is broken. Synchronises stream. */
+pt_status pt_selftest_bounded_wait(void* d_flag, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * systems); differences of two readings count the launches in between. */
 pt_status pt_launch_count(uint64_t* count);

@@ -104,6 +104,7 @@ def load() -> C.CDLL:
         "pt_get_timing": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]),
         "pt_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
         "pt_exchange_static": (C.c_int, [P, vp, vp, vp]),
+        "pt_selftest_bounded_wait": (C.c_int, [vp, vp]),
         "pt_destroy": (C.c_int, [vp]),
         "pt_last_error": (C.c_char_p, [vp]),
     }
@@ -252,6 +253,11 @@ def pt_get_timing(h, reset: bool = False) -> tuple[float, int, int]:
 def pt_exchange_static(params: PtParams, d_psi: int, d_w: int, stream: int = 0) -> None:
     """V_X Psi with no device allocation (scratch in a static 64 MiB device array)."""
     _check(load().pt_exchange_static(C.byref(params), C.c_void_p(d_psi), C.c_void_p(d_w), C.c_void_p(stream)))
+
+
+def pt_selftest_bounded_wait(d_flag: int, stream: int = 0) -> int:
+    """Run the bounded-wait self-test; returns the status (PT_ERR_TIMEOUT when the wait gave up)."""
+    return load().pt_selftest_bounded_wait(C.c_void_p(d_flag), C.c_void_p(stream))
 
 
 def pt_launch_count() -> int:

@@ -1117,6 +1117,19 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
   return st;
 }
 
+pt_status pt_selftest_bounded_wait(void* d_flag, void* stream) {
+  if (d_flag == nullptr) { g_last_error = "pt_selftest_bounded_wait: NULL flag"; return PT_ERR_INVALID; }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = pt::selftest_bounded_wait((int*)d_flag, s);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { g_last_error = "pt_selftest_bounded_wait: " + pt::cuda_msg(e); return PT_ERR_CUDA; }
+  if (h != 0) { g_last_error = "pt_selftest_bounded_wait: the wait gave up as designed"; return PT_ERR_TIMEOUT; }
+  return PT_OK;
+}
+
 pt_status pt_launch_count(uint64_t* count) {
   if (count == nullptr) return PT_ERR_INVALID;
   *count = (uint64_t)pt::launch_count();

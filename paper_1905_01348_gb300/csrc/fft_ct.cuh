@@ -187,8 +187,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
 }
 
 // Wait for phase `parity` with an iteration cap; false when the cap is hit.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, int cap = 1 << 22) {
+  for (int it = 0; it < cap; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

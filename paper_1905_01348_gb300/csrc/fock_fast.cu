@@ -265,6 +265,26 @@ static cudaError_t launch_fast(const void* psi_r, const void* x_r, void* w_occ, 
   return cudaGetLastError();
 }
 
+// Self-test of the bounded wait: one block announces a transfer that is never
+// issued and waits for it with a small cap; the wait must give up and the
+// kernel must report it through *flag (no copy is ever in flight).
+__global__ void k_selftest_wait(int* flag, int cap) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, cap);
+  if (threadIdx.x == 0) *flag = ok ? 0 : 1;
+}
+
+cudaError_t selftest_bounded_wait(int* d_flag, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(d_flag, 1 << 14);
+  launched();
+  return cudaGetLastError();
+}
+
 bool fock_fast_supported(Grid3 g) {
   return g.n0 == g.n1 && g.n1 == g.n2 && (g.n0 == 32 || g.n0 == 64 || g.n0 == 96);
 }
