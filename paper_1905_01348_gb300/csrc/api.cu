@@ -940,11 +940,7 @@ pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_wo
   st = init_body(sys, psi0_host);
   if (st != PT_OK) {
     g_last_error = sys->err;
-    std::free(sys->plan_sym.launch_first);
-    std::free(sys->plan_sym.launch_count);
-    std::free(sys->plan_x.launch_first);
-    std::free(sys->plan_x.launch_count);
-    delete sys;
+    pt_destroy(sys);
     return st;
   }
   *out = sys;

@@ -51,7 +51,7 @@ __device__ __forceinline__ void issue_slab(float2* land, const float2* slab, uns
 // read through the read-only cache), forward FFT along axis 2, store
 // X[slot][i2][i0][i1].
 template <int L>
-__global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f1(const float2* __restrict__ psi_r,
+__global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __restrict__ psi_r,
                                                           const float2* __restrict__ x_r,
                                                           const PairTile* __restrict__ tiles, int tile0,
                                                           float2* __restrict__ X, const float2* __restrict__ tw_g) {
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(Cfg<L>::NT2, 1) k_fast_f2(float2* __restrict__
 // F3: inverse FFT along axis 2 for all pairs of the tile, then each output
 // orbital adds its listed contributions to its W rows (one writer per row).
 template <int L>
-__global__ void __launch_bounds__(Cfg<L>::NT13) k_fast_f3(const float2* __restrict__ psi_r,
+__global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f3(const float2* __restrict__ psi_r,
                                                           const float2* __restrict__ x_r, float2* __restrict__ w_occ,
                                                           float2* __restrict__ w_x, const PairTile* __restrict__ tiles,
                                                           int tile0, const float2* __restrict__ X,
