@@ -69,16 +69,31 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-def pair_pipeline_bytes(n, mixed: bool, tile: int = 4) -> float:
+def live_fraction(basis_idx, n) -> float:
+    """Fraction of axis-2 frequency slabs a pair product can reach.
+
+    Products of two basis functions reach |G2| <= 2 max|g2| over the basis;
+    the other slabs are exactly zero and the FP32 cubic pair kernels skip them.
+    """
+    import numpy as np
+    n2 = int(n[2])
+    i2 = np.asarray(basis_idx) % n2
+    f = np.where(i2 < (n2 + 1) // 2, i2, i2 - n2)
+    reach = 2 * int(np.max(np.abs(f)))
+    return 1.0 if 2 * reach + 1 >= n2 else (2 * reach + 1) / n2
+
+
+def pair_pipeline_bytes(n, mixed: bool, tile: int = 4, live: float = 1.0) -> float:
     """Algorithmic HBM bytes per unordered pair of the pair pipeline.
 
-    Four passes over the pair intermediate (F1 write, F2 read + write, F3
-    read) of N complex values, plus orbital reads and W accumulation amortised
-    over a tile of `tile` x `tile` pairs: (4 + 4 / tile) * N * sizeof(complex).
+    Four passes over the live part of the pair intermediate (F1 write, F2
+    read + write, F3 read) of live * N complex values, plus orbital reads and
+    W accumulation amortised over a tile of `tile` x `tile` pairs:
+    (4 live + 4 / tile) * N * sizeof(complex).
     """
     N = int(n[0]) * int(n[1]) * int(n[2])
     cs = 8 if mixed else 16
-    return (4.0 + 4.0 / tile) * N * cs
+    return (4.0 * live + 4.0 / tile) * N * cs
 
 
 def traffic_per_launch(workload: str, precision: str):
@@ -247,15 +262,23 @@ def run_gpu(args):
     torch.cuda.nvtx.range_push("timed_steps")
     e0.record(stream)
     infos = []
-    for _ in range(args.steps):
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    step_ev[0].record(stream)
+    for k in range(args.steps):
         st, info = sysg.step()
         infos.append(info)
+        step_ev[k + 1].record(stream)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
     launches = pkg.pt_launch_count() - launches0
     clk = clocks.stop()
     t_ms = e0.elapsed_time(e1)
+    step_ms = sorted(step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps))
+
+    def pct(q):
+        import math
+        return step_ms[min(len(step_ms) - 1, max(0, math.ceil(q * len(step_ms)) - 1))]
     pair_ms, pair_count, groups = pkg.pt_get_timing(sysg.handle, reset=True)
     if ws > 1:
         import torch.distributed as dist
@@ -268,30 +291,39 @@ def run_gpu(args):
 
     # roofline of the pair pipeline (F1 + F2 + F3 of every launch group)
     peaks = measured_peaks()
-    alg_bytes_pair = pair_pipeline_bytes(w["n"], args.precision == "mixed")
+    mixed = args.precision == "mixed"
+    cubic_fast = mixed and w["n"][0] == w["n"][1] == w["n"][2] and w["n"][0] in (32, 64, 96)
+    live = live_fraction(pkg.pt_basis_indices(params), w["n"]) if cubic_fast else 1.0
+    alg_bytes_pair = pair_pipeline_bytes(w["n"], mixed, live=live)
     pair_time_s = pair_ms / 1e3
     achieved = alg_bytes_pair * pair_count / pair_time_s / 1e9 if pair_time_s > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
             "traffic": traffic_per_launch(args.workload, args.precision),
-            "kernel": "fock pair pipeline (k_fock_f1 + k_fock_f2 + k_fock_f3), one launch group = one round of tiles",
-            "launch_groups": groups, "pair_pipeline_ms": pair_ms,
+            "kernel": "fock pair pipeline (k_fast_f1 + k_fast_f2 + k_fast_f3 at 96^3, FP32), one launch group = "
+                      "one round of tiles",
+            "launch_groups": groups, "pair_pipeline_ms": pair_ms, "alg_bytes_per_pair": alg_bytes_pair,
+            "live_slab_fraction": live,
             "pairs_per_s_in_pipeline": pair_count / pair_time_s if pair_time_s > 0 else None,
             "peak_source": peaks["source"]}
 
-    # end to end through the public API with host buffers: upload orbitals,
-    # one step, download orbitals (pinned host memory)
+    # end to end through the public API with host buffers: every step loads
+    # the state (Psi_n, W_n = V_X Psi_n) from pinned host memory, steps, and
+    # stores the new state back to the same host buffers (a trajectory that
+    # lives on the host between steps, as in checkpointed or served runs)
     e2e = None
     if not args.no_e2e:
-        host_in = torch.from_numpy(sysg.orbitals()).pin_memory()
-        host_out = torch.empty_like(host_in).pin_memory()
-        nbytes = host_in.numel() * 16
+        psi_np, w_np = sysg.get_state()
+        host_psi = torch.from_numpy(psi_np).pin_memory()
+        host_w = torch.from_numpy(w_np).pin_memory()
+        hp, hw = host_psi.numpy(), host_w.numpy()
+        nbytes = 2 * host_psi.numel() * 16
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            pkg.pt_set_orbitals(sysg.handle, host_in.numpy())
+            pkg.pt_set_state(sysg.handle, hp, hw)
             sysg.step()
-            host_out.copy_(torch.from_numpy(sysg.orbitals()))
+            pkg.pt_get_state(sysg.handle, hp, hw)
         barrier()
         te = time.perf_counter() - t0
         if ws > 1:
@@ -300,9 +332,9 @@ def run_gpu(args):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
         e2e = {"value": pairs * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes + 64,
-               "note": "per step: pt_set_orbitals from pinned host memory (orthonormalise + exchange + ACE of the "
-                       "uploaded state), pt_cn_step, pt_get_orbitals to host"}
+               "d2h_bytes_per_step": nbytes,
+               "note": "per step: pt_set_state from pinned host memory (orbitals and their exchange; rebuilds ACE "
+                       "and observables), pt_cn_step, pt_get_state back to the host buffers"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -321,6 +353,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (orbitals and pair intermediates are GBs)",
                        "parallelism": f"replicas x{ws}"},
             "wall_s_per_fs": ms_per_step * STEPS_PER_FS / 1e3,
+            "step_latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "n": len(step_ms)},
             "scf_iters": [i["scf_iters"] for i in infos],
             "converged": [bool(i["converged"]) for i in infos],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

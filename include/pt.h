@@ -46,7 +46,7 @@ typedef enum pt_status {
   PT_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   PT_ERR_NOT_CONVERGED = 4,  /* SCF loop reached scf_max (state still advanced) */
   PT_ERR_NOT_PD = 5,         /* Cholesky met a non-positive pivot */
-  PT_ERR_TIMEOUT = 6         /* a bounded device wait gave up */
+  PT_ERR_TIMEOUT = 6         /* reserved: the kernels have no device-side waits */
 } pt_status;
 
 enum { PT_FP64 = 0, PT_MIXED = 1 };                       /* precision */
@@ -79,6 +79,8 @@ typedef struct pt_params {
   double relax_mix;      /* Kerker mixing weight b of the relaxation density */
   double relax_q0;       /* Kerker wavevector q0 (bohr^-1): weight b |G|^2 / (|G|^2 + q0^2) */
   int pair_tile;         /* orbitals per pair-tile edge (0 = automatic) */
+  int pair_tiles_per_launch; /* cap on pair tiles per launch group, which sizes the pair
+                              * intermediate in the workspace (0 = automatic: up to 16 GB) */
 } pt_params;
 
 typedef struct pt_system pt_system;
@@ -158,13 +160,24 @@ pt_status pt_orbitals_device(pt_system* s, void** d_psi);
 pt_status pt_set_timing(pt_system* s, int enable);
 pt_status pt_get_timing(pt_system* s, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset);
 
-/* Failure-detection self-test (no counterpart in the paper). Launches one
- * block that waits, with a small iteration cap, on an mbarrier transfer that
- * is never issued, exactly as the pair kernels wait for their bulk copies.
- * The wait gives up, the kernel writes 1 to the caller's device int d_flag,
- * and the call returns PT_ERR_TIMEOUT with the context still usable. Any
- * other status means the bounded-wait path is broken. Synchronises stream. */
-pt_status pt_selftest_bounded_wait(void* d_flag, void* stream);
+/* Checkpoint and resume (no counterpart in the paper). Between steps a
+ * system's state is its orbitals Psi_n and W = V_X Psi_n (the exchange of
+ * Eq. 3 applied to them), both npw x n_orb complex128 (interleaved re, im),
+ * band-major.
+ * pt_get_state copies both to host buffers psi_host and w_host (caller-owned,
+ * npw * n_orb complex128 each; pinned memory copies fastest) and synchronises
+ * the system's stream.
+ * pt_set_state uploads a state taken by pt_get_state from a system with the
+ * same parameters, then rebuilds from it, without an exchange, what the next
+ * step needs: the real-space orbitals, the ACE operator (-Psi^H W = L L^H,
+ * xi = W L^{-H}) and the observables. The next pt_cn_step then reproduces the
+ * original run bit for bit. Host buffers are read during the call only.
+ * Errors: PT_ERR_INVALID for NULL arguments; PT_ERR_NOT_PD when -Psi^H W is
+ * not positive definite (W is not the exchange of Psi), after which the
+ * system must be given a state again (pt_set_state or pt_set_orbitals)
+ * before it steps; PT_ERR_CUDA for a failed copy or launch. */
+pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host);
+pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * systems); differences of two readings count the launches in between. */

@@ -49,6 +49,7 @@ class PtParams(C.Structure):
         ("relax_mix", C.c_double),
         ("relax_q0", C.c_double),
         ("pair_tile", C.c_int),
+        ("pair_tiles_per_launch", C.c_int),
     ]
 
 
@@ -98,13 +99,14 @@ def load() -> C.CDLL:
         "pt_propagate": (C.c_int, [vp, C.c_int, C.POINTER(PtStepInfo)]),
         "pt_get_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
         "pt_set_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
+        "pt_get_state": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "pt_set_state": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "pt_observables": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "pt_orbitals_device": (C.c_int, [vp, C.POINTER(vp)]),
         "pt_set_timing": (C.c_int, [vp, C.c_int]),
         "pt_get_timing": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]),
         "pt_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
         "pt_exchange_static": (C.c_int, [P, vp, vp, vp]),
-        "pt_selftest_bounded_wait": (C.c_int, [vp, vp]),
         "pt_destroy": (C.c_int, [vp]),
         "pt_last_error": (C.c_char_p, [vp]),
     }
@@ -156,6 +158,7 @@ def make_params(d: dict) -> PtParams:
     p.relax_mix = float(d.get("relax_mix", 0.5))
     p.relax_q0 = float(d.get("relax_q0", 1.0))
     p.pair_tile = int(d.get("pair_tile", 0))
+    p.pair_tiles_per_launch = int(d.get("pair_tiles_per_launch", 0))
     return p
 
 
@@ -225,6 +228,28 @@ def pt_set_orbitals(h, psi: np.ndarray) -> None:
     _check(load().pt_set_orbitals(h, psi.ctypes.data_as(C.POINTER(C.c_double))), h)
 
 
+def _host_c128(a: np.ndarray, shape, name: str) -> np.ndarray:
+    if a.dtype != np.complex128 or not a.flags.c_contiguous or a.shape != tuple(shape):
+        raise ValueError(f"{name}: expected a C-contiguous complex128 array of shape {tuple(shape)}")
+    return a
+
+
+def pt_get_state(h, psi_out: np.ndarray, w_out: np.ndarray) -> None:
+    """Copy the state (Psi, W = V_X Psi) into caller-owned (n_orb, npw) complex128 arrays."""
+    _host_c128(psi_out, w_out.shape, "psi_out")
+    _host_c128(w_out, psi_out.shape, "w_out")
+    _check(load().pt_get_state(h, psi_out.ctypes.data_as(C.POINTER(C.c_double)),
+                               w_out.ctypes.data_as(C.POINTER(C.c_double))), h)
+
+
+def pt_set_state(h, psi: np.ndarray, w: np.ndarray) -> None:
+    """Resume from a state taken by pt_get_state (same parameters)."""
+    _host_c128(psi, w.shape, "psi")
+    _host_c128(w, psi.shape, "w")
+    _check(load().pt_set_state(h, psi.ctypes.data_as(C.POINTER(C.c_double)),
+                               w.ctypes.data_as(C.POINTER(C.c_double))), h)
+
+
 def pt_observables(h) -> tuple[float, np.ndarray]:
     e = C.c_double(0.0)
     d = (C.c_double * 3)()
@@ -253,11 +278,6 @@ def pt_get_timing(h, reset: bool = False) -> tuple[float, int, int]:
 def pt_exchange_static(params: PtParams, d_psi: int, d_w: int, stream: int = 0) -> None:
     """V_X Psi with no device allocation (scratch in a static 64 MiB device array)."""
     _check(load().pt_exchange_static(C.byref(params), C.c_void_p(d_psi), C.c_void_p(d_w), C.c_void_p(stream)))
-
-
-def pt_selftest_bounded_wait(d_flag: int, stream: int = 0) -> int:
-    """Run the bounded-wait self-test; returns the status (PT_ERR_TIMEOUT when the wait gave up)."""
-    return load().pt_selftest_bounded_wait(C.c_void_p(d_flag), C.c_void_p(stream))
 
 
 def pt_launch_count() -> int:

@@ -126,6 +126,7 @@ static pt_status check_params(const pt_params* p, std::string* why) {
   if (p->fock_mode != PT_FOCK_EXACT && p->fock_mode != PT_FOCK_ACE) { *why = "fock_mode"; return PT_ERR_INVALID; }
   if (!(p->omega > 0.0)) { *why = "omega must be positive"; return PT_ERR_INVALID; }
   if (p->pair_tile < 0 || p->pair_tile > pt::kTileMax) { *why = "pair_tile must be in [0, 4]"; return PT_ERR_INVALID; }
+  if (p->pair_tiles_per_launch < 0) { *why = "pair_tiles_per_launch must be >= 0"; return PT_ERR_INVALID; }
   if (p->scf_max < 1 && p->scf_fixed_iters < 1) { *why = "scf_max or scf_fixed_iters must be >= 1"; return PT_ERR_INVALID; }
   return PT_OK;
 }
@@ -150,6 +151,15 @@ static void basis_list(const pt_params* p, std::vector<int>* idx, std::vector<do
       }
 }
 
+// Twice the largest |g2| over the basis: the reach of pair products along axis 2.
+static int pair_g2_reach(const pt_params* p) {
+  std::vector<int> idx;
+  basis_list(p, &idx, nullptr);
+  int m = 0;
+  for (int v : idx) m = std::max(m, std::abs(freq(v % p->n[2], p->n[2])));
+  return 2 * m;
+}
+
 static int choose_tile(const pt_params* p) {
   if (p->pair_tile > 0) return p->pair_tile;
   return std::min(pt::kTileMax, p->n_orb);
@@ -161,6 +171,7 @@ static int tiles_per_launch(const pt_params* p, long N, bool mixed) {
   const double per_tile = (double)pt::kTileMax * pt::kTileMax * N * (mixed ? 8.0 : 16.0);
   const double budget = 16.0e9;
   int cap = (int)std::max(1.0, std::floor(budget / per_tile));
+  if (p->pair_tiles_per_launch > 0) cap = std::min(cap, p->pair_tiles_per_launch);
   return std::max(1, std::min(nb, cap));
 }
 
@@ -329,18 +340,6 @@ static pt_status apply_local(pt_system* sys, const double2* X, double2* out, int
 }
 
 // V_X Psi for the orbitals whose real-space form is in psi_r; out = (or +=) result
-// A bounded device wait in the pair kernels that gave up leaves 1 in the flag.
-static pt_status check_pair_flag(pt_system* sys) {
-  int h = 0;
-  PT_CK(cudaMemcpyAsync(&h, sys->plan_sym.d_err, sizeof(int), cudaMemcpyDeviceToHost, sys->s));
-  PT_CK(cudaStreamSynchronize(sys->s));
-  if (h != 0) {
-    sys->err = "exchange: a pair kernel timed out waiting for a bulk copy";
-    return PT_ERR_TIMEOUT;
-  }
-  return PT_OK;
-}
-
 template <typename T>
 static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
   const size_t cs = sizeof(pt::cplx<T>);
@@ -358,7 +357,6 @@ static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
     sys->t_pairs += (long long)sys->ne * (sys->ne + 1) / 2;
     sys->t_groups += sys->plan_sym.n_launch;
   }
-  PT_TRY(check_pair_flag(sys));
   return to_basis<T>(sys, sys->w_r, sys->ne, out, accumulate, nullptr, nullptr);
 }
 
@@ -394,7 +392,7 @@ static pt_status ensure_plan_x(pt_system* sys, int ncols) {
   sys->plan_x.launch_count = lc;
   sys->plan_x.d_tiles = sys->d_tiles_x;
   sys->plan_x.n_tiles = nt;
-  sys->plan_x.d_err = sys->status + 4;
+  sys->plan_x.g2_reach = pair_g2_reach(&sys->p);
   sys->plan_x_ncols = ncols;
   return PT_OK;
 }
@@ -408,7 +406,6 @@ static pt_status exchange_x_t(pt_system* sys, const double2* X, int ncols, doubl
   const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
   const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
   PT_CK(pt::fock_pairs<T>(pr, sys->x_r, nullptr, sys->w_r, sys->plan_x, 0, sys->g, kt, sys->scratch, sys->tw, sys->s));
-  PT_TRY(check_pair_flag(sys));
   return to_basis<T>(sys, sys->w_r, ncols, out, 1, nullptr, nullptr);
 }
 
@@ -485,9 +482,10 @@ static pt_status orthonormalize(pt_system* sys, const double2* src, double2* dst
 }
 
 // exchange data of psi (psi_r current): wg = V_X psi, Mneg = -psi^H wg, ACE
-static pt_status exchange_data(pt_system* sys) {
+// ACE data of the current (psi, wg): Mneg = -Psi^H W; Cholesky -M = L L^H;
+// xi = W L^{-H} (ACE construction following Eq. 3 and the ACE definition).
+static pt_status ace_from_w(pt_system* sys) {
   const int ne = sys->ne, npw = sys->npw;
-  PT_TRY(exchange_sym(sys, sys->wg, 0));
   const bool ace = sys->p.fock_mode == PT_FOCK_ACE && sys->p.alpha != 0.0;
   if (sys->mixed && ace)
     PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kMinusOne, sys->psi, npw, sys->wg, npw, kZero, sys->Mneg, ne));
@@ -507,6 +505,11 @@ static pt_status exchange_data(pt_system* sys) {
     PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->wg, npw, sys->Linv, ne, kZero, sys->xi, npw));
   sys->have_ace = true;
   return PT_OK;
+}
+
+static pt_status exchange_data(pt_system* sys) {
+  PT_TRY(exchange_sym(sys, sys->wg, 0));
+  return ace_from_w(sys);
 }
 
 // out += -xi (xi^H X)
@@ -767,7 +770,7 @@ static pt_status exchange_static_body(pt_system* t, const pt_params* p, const st
   t->plan_sym.launch_count = lc;
   t->plan_sym.n_tiles = nt;
   t->plan_sym.d_tiles = t->d_tiles_sym;
-  t->plan_sym.d_err = t->status + 4;
+  t->plan_sym.g2_reach = pair_g2_reach(p);
   PT_CK(cudaMemsetAsync(t->status, 0, sizeof(int) * 16, s));
   cudaError_t e = cudaMemcpyAsync(t->d_tiles_sym, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -889,7 +892,7 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
     sys->plan_sym.launch_count = lc;
     sys->plan_sym.d_tiles = sys->d_tiles_sym;
     sys->plan_sym.n_tiles = nt;
-    sys->plan_sym.d_err = sys->status + 4;
+    sys->plan_sym.g2_reach = pair_g2_reach(p);
   }
   PT_CK(cudaMemsetAsync(sys->status, 0, sizeof(int) * 16, s));
   PT_CK(cudaStreamSynchronize(s));
@@ -1033,6 +1036,28 @@ pt_status pt_set_orbitals(pt_system* sys, const double* psi_host) {
   return PT_OK;
 }
 
+pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host) {
+  if (sys == nullptr || psi_host == nullptr || w_host == nullptr) return PT_ERR_INVALID;
+  const size_t bytes = sizeof(double2) * sys->npw * sys->ne;
+  PT_CK(cudaMemcpyAsync(psi_host, sys->psi, bytes, cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaMemcpyAsync(w_host, sys->wg, bytes, cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
+pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host) {
+  if (sys == nullptr || psi_host == nullptr || w_host == nullptr) return PT_ERR_INVALID;
+  const size_t bytes = sizeof(double2) * sys->npw * sys->ne;
+  PT_CK(cudaMemcpyAsync(sys->psi, psi_host, bytes, cudaMemcpyHostToDevice, sys->s));
+  PT_CK(cudaMemcpyAsync(sys->wg, w_host, bytes, cudaMemcpyHostToDevice, sys->s));
+  PT_TRY(real_orbitals(sys, sys->psi));
+  sys->psi_r_current = true;
+  PT_TRY(ace_from_w(sys));
+  PT_TRY(observables(sys));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  return PT_OK;
+}
+
 pt_status pt_observables(pt_system* sys, double* energy, double* dipole) {
   if (sys == nullptr) return PT_ERR_INVALID;
   if (energy) *energy = sys->energy;
@@ -1111,19 +1136,6 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
   t.plan_sym.launch_count = nullptr;
   if (st != PT_OK) g_last_error = t.err;
   return st;
-}
-
-pt_status pt_selftest_bounded_wait(void* d_flag, void* stream) {
-  if (d_flag == nullptr) { g_last_error = "pt_selftest_bounded_wait: NULL flag"; return PT_ERR_INVALID; }
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = pt::selftest_bounded_wait((int*)d_flag, s);
-  int h = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { g_last_error = "pt_selftest_bounded_wait: " + pt::cuda_msg(e); return PT_ERR_CUDA; }
-  if (h != 0) { g_last_error = "pt_selftest_bounded_wait: the wait gave up as designed"; return PT_ERR_TIMEOUT; }
-  return PT_OK;
 }
 
 pt_status pt_launch_count(uint64_t* count) {

@@ -62,14 +62,27 @@ template <> struct Plan2<96> { static constexpr int R1 = 8, R2 = 12; };
 // on 16 distinct bank pairs for row- and column-wise stages alike, and the
 // twiddle index is uniform across the warp (a shared-memory broadcast).
 
-// One Stockham stage over lines [line0, line0 + nl) of length L. Element e of
-// line l of `src` is src[l * SLS + e * SES]; the output goes to `dst` with
-// strides (DLS, DES). src == dst gives the in-place form (all reads of the
-// stage finish before the first write). Lines at or beyond nl are skipped
-// (NL is the compile-time line capacity of one call).
-template <typename C, bool INV, int L, int R, int NS, int NL, int NT, int SLS, int SES, int DLS, int DES>
-__device__ __forceinline__ void ct_stage_io(const C* src, C* dst, int nl, const C* __restrict__ tw, int tid,
-                                            int line0 = 0) {
+// Shared-memory layouts: Strided<LS, ES> puts element e of line l at
+// l * LS + e * ES. PairRows<L> holds the lines (pair p, grid row r) of a
+// pair tile as [p][e][r] with a pair stride of 4 L + 4: a half-warp of
+// consecutive lines covers 4 pairs x 4 rows at 16 distinct bank pairs, and
+// the 4 rows of one element are contiguous (16-byte vector moves).
+template <int LS, int ES> struct Strided {
+  __device__ __forceinline__ static int at(int l, int e) { return l * LS + e * ES; }
+};
+template <int L> struct PairRows {
+  static constexpr int PS = 4 * L + 4;
+  static constexpr int SIZE = 16 * PS;
+  __device__ __forceinline__ static int at(int l, int e) { return (l >> 2) * PS + (l & 3) + e * 4; }
+};
+
+// One Stockham stage over lines [line0, line0 + nl) of length L, reading
+// through layout SA from `src` and writing through layout DA to `dst`
+// (src == dst: in place; every read of the stage finishes before the first
+// write). Lines at or beyond nl are skipped (NL is the per-call capacity).
+template <typename C, bool INV, int L, int R, int NS, int NL, int NT, class SA, class DA>
+__device__ __forceinline__ void ct_stage_lay(const C* src, C* dst, int nl, const C* __restrict__ tw, int tid,
+                                             int line0 = 0) {
   constexpr int NBL = L / R;
   constexpr int MB = (NL * NBL + NT - 1) / NT;
   constexpr int TWS = L / (NS * R);
@@ -79,9 +92,9 @@ __device__ __forceinline__ void ct_stage_io(const C* src, C* dst, int nl, const 
     const int b = tid + q * NT;
     const int ll = b % NL, j = b / NL;
     if (j < NBL && ll < nl) {
-      const int base = (line0 + ll) * SLS;
+      const int line = line0 + ll;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = src[base + (j + r * NBL) * SES];
+      for (int r = 0; r < R; ++r) v[q][r] = src[SA::at(line, j + r * NBL)];
       if (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -100,14 +113,34 @@ __device__ __forceinline__ void ct_stage_io(const C* src, C* dst, int nl, const 
     const int b = tid + q * NT;
     const int ll = b % NL, j = b / NL;
     if (j < NBL && ll < nl) {
-      const int base = (line0 + ll) * DLS;
+      const int line = line0 + ll;
       const int k = j % NS;
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[base + (o + r * NS) * DES] = v[q][r];
+      for (int r = 0; r < R; ++r) dst[DA::at(line, o + r * NS)] = v[q][r];
     }
   }
   __syncthreads();
+}
+
+template <typename C, bool INV, int L, int R, int NS, int NL, int NT, int SLS, int SES, int DLS, int DES>
+__device__ __forceinline__ void ct_stage_io(const C* src, C* dst, int nl, const C* __restrict__ tw, int tid,
+                                            int line0 = 0) {
+  ct_stage_lay<C, INV, L, R, NS, NL, NT, Strided<SLS, SES>, Strided<DLS, DES>>(src, dst, nl, tw, tid, line0);
+}
+
+template <typename C, int L, int NL, int NT, class A>
+__device__ __forceinline__ void ct_forward_lay(C* buf, int nl, const C* tw, int tid) {
+  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
+  ct_stage_lay<C, false, L, R1, 1, NL, NT, A, A>(buf, buf, nl, tw, tid);
+  ct_stage_lay<C, false, L, R2, R1, NL, NT, A, A>(buf, buf, nl, tw, tid);
+}
+
+template <typename C, int L, int NL, int NT, class A>
+__device__ __forceinline__ void ct_inverse_lay(C* buf, int nl, const C* tw, int tid) {
+  constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
+  ct_stage_lay<C, true, L, R2, 1, NL, NT, A, A>(buf, buf, nl, tw, tid);
+  ct_stage_lay<C, true, L, R1, R2, NL, NT, A, A>(buf, buf, nl, tw, tid);
 }
 
 template <typename C, bool INV, int L, int R, int NS, int NL, int NT, int LS, int ES>
@@ -153,48 +186,6 @@ __device__ __forceinline__ void ct_fused(C* buf, int nl, const C* __restrict__ t
   }
   __syncthreads();
 }
-
-// ---- bulk copies (TMA, non-tensor) and mbarriers --------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// one arrival that also announces `bytes` of incoming transaction
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// global -> shared bulk copy completing on `bar`; addresses 16-byte aligned, bytes % 16 == 0
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-               : "=r"(ok)
-               : "r"(smem_u32(bar)), "r"(parity)
-               : "memory");
-  return ok != 0;
-}
-
-// Wait for phase `parity` with an iteration cap; false when the cap is hit.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, int cap = 1 << 22) {
-  for (int it = 0; it < cap; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-// order earlier generic-proxy accesses of shared memory before later async-proxy ones
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Full forward (plan R1, R2) and inverse (plan R2, R1) line transforms in place.
 template <typename C, int L, int NL, int NT, int LS, int ES>

@@ -78,15 +78,17 @@ struct FockPlan {
   int* launch_count;
   PairTile* d_tiles;      // device
   int n_tiles;
-  int* d_err;             // device flag set to 1 when a bounded wait in a pair kernel gives up
+  // Largest |G2| (frequency index along axis 2) a pair product can reach: twice
+  // the largest |g2| of the basis. Products of band-limited orbitals vanish
+  // exactly beyond it on an alias-free grid, so the fast path skips those
+  // axis-2 slabs. A value >= n2 / 2 disables the skip.
+  int g2_reach;
 };
 
 template <typename T>
 cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
                        Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s);
 size_t fock_scratch_elems(const FockPlan& plan, Grid3 g);
-// Bounded-wait self-test (fock_fast.cu): *d_flag = 1 when the wait gave up.
-cudaError_t selftest_bounded_wait(int* d_flag, cudaStream_t s);
 // FP32 cubic fast path (fock_fast.cu): n0 == n1 == n2 in {32, 64, 96}.
 bool fock_fast_supported(Grid3 g);
 cudaError_t fock_pairs_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, Grid3 g,

@@ -34,6 +34,16 @@ class System:
     def set_orbitals(self, psi: np.ndarray) -> None:
         nat.pt_set_orbitals(self.handle, psi)
 
+    def get_state(self):
+        """(Psi, W = V_X Psi) as two (n_orb, npw) complex128 host arrays."""
+        psi = np.empty((self.n_orb, self.npw), dtype=np.complex128)
+        w = np.empty_like(psi)
+        nat.pt_get_state(self.handle, psi, w)
+        return psi, w
+
+    def set_state(self, psi: np.ndarray, w: np.ndarray) -> None:
+        nat.pt_set_state(self.handle, psi, w)
+
     def observables(self):
         return nat.pt_observables(self.handle)
 
