@@ -632,7 +632,8 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
     sl.k = (int)sys->and_order.size();
     for (int q = 0; q < sl.k; ++q) sl.s[q] = sys->and_order[q];
     if (sl.k > 0) {
-      PT_CK(pt::anderson_dots(sys->dR, stride, sl, newslot, sys->rbuf, npw, ne, m, sys->gram, sys->rhs, sys->s));
+      PT_CK(pt::anderson_dots(sys->dR, stride, sl, newslot, sys->rbuf, npw, ne, m, sys->gram, sys->rhs,
+                              sys->mixed ? 1 : 0, sys->s));
       PT_CK(pt::anderson_solve(sys->gram, sys->rhs, sl, m, ne, sys->gamma, sys->s));
     }
     PT_CK(pt::anderson_update(sys->psi_f, sys->rbuf, sys->dX, sys->dR, stride, sl, sys->gamma, std::max(m, 1), npw, n,

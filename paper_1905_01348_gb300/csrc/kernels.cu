@@ -2,8 +2,9 @@
 // Sec. 3.4) and of the local part of the Hamiltonian (Eq. 2).
 // Reductions are two-level (block partials, then one block sums the
 // partials in order), so every sum is deterministic.
-#include <cmath>
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -60,12 +61,21 @@ cudaError_t density(const double2* psi_r, long N, int ne, double* rho, cudaStrea
   return cudaGetLastError();
 }
 
+// FP32 squares summed in FP32 over groups of 16 bands (eight loads in flight
+// per thread), the group sums accumulated in FP64: FP64 work drops 16-fold.
 __global__ void k_density32(const float2* __restrict__ psi_r, long N, int ne, double* __restrict__ rho) {
+  constexpr int G = 16;
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < N; r += (long)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < ne; ++k) {
-      const float2 v = psi_r[(long)k * N + r];
-      s += (double)v.x * v.x + (double)v.y * v.y;
+    for (int k0 = 0; k0 < ne; k0 += G) {
+      const int kn = min(G, ne - k0);
+      float g = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < kn; ++k) {
+        const float2 v = __ldg(psi_r + (long)(k0 + k) * N + r);
+        g = fmaf(v.x, v.x, fmaf(v.y, v.y, g));
+      }
+      s += (double)g;
     }
     rho[r] = 2.0 * s;
   }
@@ -240,9 +250,15 @@ cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, doubl
 // conjugate at [new][slot_q]) and rhs[b][q] = <dR_{slot_q}, r>_b for the
 // history slots in order (oldest first). One block per band; the slots are
 // processed four at a time to bound registers.
+// F32 (mixed precision): the products are formed in FP32 from FP32 copies of
+// the FP64 vectors and summed in FP32 over each thread's share of the basis
+// (about npw / 256 terms); the per-thread sums are reduced in FP64. FP64
+// otherwise. The Gram matrix and right-hand side feed the FP64 solve either way.
+template <bool F32>
 __global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride, SlotList sl, int newslot,
                                 const double2* __restrict__ r, int npw, int mdim, double2* __restrict__ gram,
                                 double2* __restrict__ rhs) {
+  using A = typename std::conditional<F32, float, double>::type;
   const int b = blockIdx.x;
   const int k = sl.k;
   const long boff = (long)b * npw;
@@ -251,25 +267,27 @@ __global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride
   __shared__ double sh[16][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q0 = 0; q0 < k; q0 += 4) {
-    double acc[16];
+    A acc[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int c = 0; c < 16; ++c) acc[c] = (A)0;
     for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-      const double2 vn = dn[g], vr = rb[g];
+      const double2 vnd = dn[g], vrd = rb[g];
+      const A vnx = (A)vnd.x, vny = (A)vnd.y, vrx = (A)vrd.x, vry = (A)vrd.y;
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) {
         if (q0 + qq < k) {
-          const double2 u = dR[(long)sl.s[q0 + qq] * slot_stride + boff + g];
-          acc[4 * qq + 0] += u.x * vn.x + u.y * vn.y;
-          acc[4 * qq + 1] += u.x * vn.y - u.y * vn.x;
-          acc[4 * qq + 2] += u.x * vr.x + u.y * vr.y;
-          acc[4 * qq + 3] += u.x * vr.y - u.y * vr.x;
+          const double2 ud = dR[(long)sl.s[q0 + qq] * slot_stride + boff + g];
+          const A ux = (A)ud.x, uy = (A)ud.y;
+          acc[4 * qq + 0] += ux * vnx + uy * vny;
+          acc[4 * qq + 1] += ux * vny - uy * vnx;
+          acc[4 * qq + 2] += ux * vrx + uy * vry;
+          acc[4 * qq + 3] += ux * vry - uy * vrx;
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      double x = acc[c];
+      double x = (double)acc[c];
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
       if (lane == 0) sh[c][warp] = x;
     }
@@ -297,9 +315,11 @@ __global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride
 }
 
 cudaError_t anderson_dots(const double2* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
-                          int npw, int ne, int mdim, double2* gram, double2* rhs, cudaStream_t s) {
+                          int npw, int ne, int mdim, double2* gram, double2* rhs, int f32, cudaStream_t s) {
   if (sl.k > kSlotMax) return cudaErrorInvalidValue;
-  k_anderson_dots<<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs); launched();
+  if (f32) k_anderson_dots<true><<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
+  else k_anderson_dots<false><<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
+  launched();
   return cudaGetLastError();
 }
 

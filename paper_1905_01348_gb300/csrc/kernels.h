@@ -28,7 +28,8 @@ cudaError_t precond_step(double2* x, const double2* R, const double* kin, int np
 cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, double2* dx, double2* dr,
                           long n, int have_prev, cudaStream_t s);
 cudaError_t anderson_dots(const double2* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
-                          int npw, int ne, int mdim, double2* gram, double2* rhs, cudaStream_t s);
+                          int npw, int ne, int mdim, double2* gram, double2* rhs, int f32,
+                          cudaStream_t s);
 cudaError_t anderson_solve(const double2* gram, const double2* rhs, const SlotList& sl, int mdim, int ne,
                            double2* gamma, cudaStream_t s);
 cudaError_t anderson_update(double2* x, const double2* r, const double2* dX, const double2* dR, long slot_stride,
