@@ -48,6 +48,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the pair products have no component there (the slab stays unwritten in X).
 template <int L> __device__ __forceinline__ bool dead_slab(int i2, int reach) { return i2 > reach && i2 < L - reach; }
 
+// An off-diagonal tile of two full orbital blocks: orbitals 0..3 and 4..7,
+// pair 4a + b = (a, 4 + b).
+__device__ __forceinline__ bool full_tile(const PairTile& tl) { return tl.n_orb == 2 * TT && tl.n_pairs == NPAIR; }
+
 __device__ __forceinline__ const float2* orb_ptr(const PairTile& tl, int o, const float2* psi_r, const float2* x_r,
                                                  long N) {
   return (tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N;
@@ -82,38 +86,52 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
   const int i1s = (blockIdx.x % NB1) * RR;
   const long roff = ((long)i0 * L + i1s) * L;
   const int np = tl.n_pairs;
-  // four products per thread per round: all eight loads are issued before the first use
-  constexpr int U = 4;
-  for (int base = tid; base < np * ROW; base += U * NT) {
-    float2 a[U], b[U];
+  if (full_tile(tl)) {
+    // off-diagonal 4 x 4 tile: pair 4a + b is (a, 4 + b); the eight orbital
+    // values of an element are loaded once (eight loads in flight)
+    for (int e = tid; e < ROW; e += NT) {
+      float2 v[2 * TT];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * NT;
-      if (idx < np * ROW) {
-        const int p = idx / ROW, e = idx % ROW;
-        a[u] = __ldg(orb_ptr(tl, tl.pi[p], psi_r, x_r, N) + roff + e);
-        b[u] = __ldg(orb_ptr(tl, tl.pj[p], psi_r, x_r, N) + roff + e);
-      }
+      for (int o = 0; o < 2 * TT; ++o) v[o] = __ldg(orb_ptr(tl, o, psi_r, x_r, N) + roff + e);
+      const int row = e / L, col = e % L;
+#pragma unroll
+      for (int a = 0; a < TT; ++a)
+#pragma unroll
+        for (int b = 0; b < TT; ++b) work[A::at((a * TT + b) * RR + row, col)] = cmulc(v[a], v[TT + b]);
     }
+  } else {
+    // any tile: four products per thread per round, all eight loads issued before the first use
+    constexpr int U = 4;
+    for (int base = tid; base < np * ROW; base += U * NT) {
+      float2 a[U], b[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * NT;
-      if (idx < np * ROW) {
-        const int p = idx / ROW, e = idx % ROW;
-        work[A::at(p * RR + e / L, e % L)] = cmulc(a[u], b[u]);
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT;
+        if (idx < np * ROW) {
+          const int p = idx / ROW, e = idx % ROW;
+          a[u] = __ldg(orb_ptr(tl, tl.pi[p], psi_r, x_r, N) + roff + e);
+          b[u] = __ldg(orb_ptr(tl, tl.pj[p], psi_r, x_r, N) + roff + e);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT;
+        if (idx < np * ROW) {
+          const int p = idx / ROW, e = idx % ROW;
+          work[A::at(p * RR + e / L, e % L)] = cmulc(a[u], b[u]);
+        }
       }
     }
   }
   __syncthreads();
   ct_forward_lay<float2, L, NPAIR * RR, NT, A>(work, np * RR, tw, tid);
+  // lanes: r fastest, then i2, so each (pair, i2) writes one run of RR values along i1
   const long slot0 = (long)blockIdx.y * NPAIR;
-  for (int idx = tid; idx < np * ROW; idx += NT) {
-    const int r = idx % RR;
-    const int rest = idx / RR;
-    const int i2 = rest % L;
-    const int p = rest / L;
-    if (dead_slab<L>(i2, reach)) continue;
-    X[(((slot0 + p) * L + i2) * L + i0) * L + i1s + r] = work[A::at(p * RR + r, i2)];
+  const int r = tid % RR;
+  for (int p = 0; p < np; ++p) {
+    float2* xp = X + (slot0 + p) * N + (long)i0 * L + i1s + r;
+    for (int i2 = tid / RR; i2 < L; i2 += NT / RR)
+      if (!dead_slab<L>(i2, reach)) xp[(long)i2 * L * L] = work[A::at(p * RR + r, i2)];
   }
 }
 
@@ -200,21 +218,51 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f3(const float2* __res
   const long roff = ((long)i0 * L + i1s) * L;
   const int np = tl.n_pairs;
   const long slot0 = (long)blockIdx.y * NPAIR;
-  for (int idx = tid; idx < np * ROW; idx += NT) {
-    const int r = idx % RR;
-    const int rest = idx / RR;
-    const int i2 = rest % L;
-    const int p = rest / L;
-    float2* dst = work + A::at(p * RR + r, i2);
-    if (dead_slab<L>(i2, reach)) {
-      *dst = make_float2(0.f, 0.f);
-    } else {
-      cp_async8(dst, X + (((slot0 + p) * L + i2) * L + i0) * L + i1s + r);
+  const int r = tid % RR;
+  for (int p = 0; p < np; ++p) {
+    const float2* xp = X + (slot0 + p) * N + (long)i0 * L + i1s + r;
+    for (int i2 = tid / RR; i2 < L; i2 += NT / RR) {
+      float2* dst = work + A::at(p * RR + r, i2);
+      if (dead_slab<L>(i2, reach)) *dst = make_float2(0.f, 0.f);
+      else cp_async8(dst, xp + (long)i2 * L * L);
     }
   }
   cp_async_wait_all();
   __syncthreads();
   ct_inverse_lay<float2, L, NPAIR * RR, NT, A>(work, np * RR, tw, tid);
+  if (full_tile(tl)) {
+    // off-diagonal 4 x 4 tile: output a (< 4) takes psi_{4+b} conj(v_ab) over b, output
+    // 4 + b takes psi_a v_ab over a, in the order of the contribution lists; all orbital
+    // and W loads of an element are issued together
+    for (int e = tid; e < ROW; e += NT) {
+      const int row = e / L, col = e % L;
+      float2 v[2 * TT], w[2 * TT];
+      float2* dst[2 * TT];
+#pragma unroll
+      for (int o = 0; o < 2 * TT; ++o) {
+        v[o] = __ldg(orb_ptr(tl, o, psi_r, x_r, N) + roff + e);
+        dst[o] = (tl.src[o] == 0 ? w_occ : w_x) + (long)tl.orb[o] * N + roff + e;
+        if (tl.is_out[o]) w[o] = *dst[o];
+      }
+#pragma unroll
+      for (int a = 0; a < TT; ++a) {
+        if (!tl.is_out[a]) continue;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < TT; ++b) acc = cadd(acc, cmul_conj(v[TT + b], work[A::at((a * TT + b) * RR + row, col)]));
+        *dst[a] = cadd(w[a], acc);
+      }
+#pragma unroll
+      for (int b = 0; b < TT; ++b) {
+        if (!tl.is_out[TT + b]) continue;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < TT; ++a) acc = cadd(acc, cmul(v[a], work[A::at((a * TT + b) * RR + row, col)]));
+        *dst[TT + b] = cadd(w[TT + b], acc);
+      }
+    }
+    return;
+  }
   for (int o = 0; o < tl.n_orb; ++o) {
     const int n = tl.out_n[o];
     if (!tl.is_out[o] || n == 0) continue;

@@ -134,3 +134,20 @@ def test_exchange_mixed_large_grids(pkg, name, n_orb):
     s = pkg.System(w, C0)
     assert rel(s.exchange().cpu().numpy().T, st.W) < 2e-5
     s.close()
+
+
+def test_apply_h_exact_mixed_cubic(pkg):
+    """V_X applied to vectors other than the orbitals on the 32^3 FP32 pair path:
+    non-symmetric tiles (full 4 x 4 and ragged 4 x 1), only the X side accumulates."""
+    import torch
+    w = syn.si_workload("si8", relax_iters=0, precision="mixed", fock_mode="exact")
+    model, C0 = make(w, seed=4)
+    st = model.init_state(C0)
+    X = syn.gaussian_vectors((model.grid.npw, 5), seed=11)
+    ref = model.vx(st.Psi, X)
+    s = pkg.System(w, C0)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.T)).to("cuda:0")
+    # the exchange part alone: H X with and without V_X (the local part is FP64 in both)
+    Y = (s.apply_h(Xd, pkg.PT_FOCK_EXACT) - s.apply_h(Xd, pkg.PT_FOCK_NONE)).cpu().numpy().T
+    assert rel(Y, ref) < 2e-5
+    s.close()
