@@ -67,6 +67,9 @@ struct pt_system {
   double2* hbuf = nullptr;
   double2* psi_r = nullptr;
   float2* psi_r32 = nullptr;
+  // complex64 copies for the FP32 products of mixed precision: xi (per step) and two
+  // operand staging buffers (n_orb x npw) plus one n_orb x n_orb buffer
+  float2 *xi32 = nullptr, *ga32 = nullptr, *gb32 = nullptr, *gs32 = nullptr;
   void *w_r = nullptr, *x_r = nullptr, *scratch = nullptr;
   double2 *S = nullptr, *Mneg = nullptr, *Linv = nullptr, *Z = nullptr, *gemm_ws = nullptr;
   size_t gemm_ws_elems = 0;
@@ -225,6 +228,12 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   t->hbuf = c.take<double2>((size_t)N * hb);
   t->psi_r = c.take<double2>((size_t)N * ne);
   if (mixed) t->psi_r32 = c.take<float2>((size_t)N * ne);
+  if (mixed) {
+    t->xi32 = c.take<float2>(pe);
+    t->ga32 = c.take<float2>(pe);
+    t->gb32 = c.take<float2>(pe);
+    t->gs32 = c.take<float2>(ne * ne);
+  }
   t->w_r = c.take<unsigned char>((size_t)N * ne * cs);
   t->x_r = c.take<unsigned char>((size_t)N * ne * cs);
   t->scratch = c.take<unsigned char>((size_t)tpl * pt::kTileMax * pt::kTileMax * N * cs);
@@ -411,13 +420,28 @@ static pt_status exchange_x_t(pt_system* sys, const double2* X, int ncols, doubl
 
 template <typename Tc>
 static pt_status gemm(pt_system* sys, int opA, int opB, int M, int N, int K, double2 alpha, const double2* A, long lda,
-                      const double2* B, long ldb, double2 beta, double2* C, long ldc) {
+                      const double2* B, long ldb, double2 beta, double2* C, long ldc,
+                      int structure = pt::GEMM_GENERAL) {
   PT_CK(pt::gemm<Tc>(opA, opB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1, sys->gemm_ws,
-                     sys->gemm_ws_elems, sys->s));
+                     sys->gemm_ws_elems, sys->s, structure));
   return PT_OK;
 }
 
 static const double2 kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMinusOne = {-1.0, 0.0};
+
+// FP32 product of complex64 copies (mixed precision); C stays complex128.
+static pt_status gemm32(pt_system* sys, int opA, int opB, int M, int N, int K, double2 alpha, const float2* A, long lda,
+                        const float2* B, long ldb, double2 beta, double2* C, long ldc,
+                        int structure = pt::GEMM_GENERAL) {
+  PT_CK(pt::gemm_c64(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sys->gemm_ws, sys->gemm_ws_elems, sys->s,
+                     structure));
+  return PT_OK;
+}
+
+static pt_status to32(pt_system* sys, const double2* src, float2* dst, long n) {
+  PT_CK(pt::convert_c128_to_c64(src, dst, n, sys->s));
+  return PT_OK;
+}
 
 // SCF-iteration forms. In mixed precision the real-space orbitals, the
 // density they give and the local-potential product run in FP32; in FP64
@@ -453,8 +477,11 @@ static pt_status apply_local_scf(pt_system* sys, const double2* c, double2* out)
 static pt_status projection(pt_system* sys, const double2* A, double2* HB) {
   const int ne = sys->ne, npw = sys->npw;
   if (sys->mixed) {
-    PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, A, npw, HB, npw, kZero, sys->S, ne));
-    PT_TRY(gemm<float>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, A, npw, sys->S, ne, kOne, HB, npw));
+    PT_TRY(to32(sys, A, sys->ga32, (long)npw * ne));
+    PT_TRY(to32(sys, HB, sys->gb32, (long)npw * ne));
+    PT_TRY(gemm32(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, sys->ga32, npw, sys->gb32, npw, kZero, sys->S, ne));
+    PT_TRY(to32(sys, sys->S, sys->gs32, (long)ne * ne));
+    PT_TRY(gemm32(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, sys->ga32, npw, sys->gs32, ne, kOne, HB, npw));
   } else {
     PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, A, npw, HB, npw, kZero, sys->S, ne));
     PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ne, ne, kMinusOne, A, npw, sys->S, ne, kOne, HB, npw));
@@ -471,25 +498,28 @@ static pt_status read_status(pt_system* sys, int* h) {
 // dst = src L^{-H}, L L^H = src^H src  (Sec. 3.4)
 static pt_status orthonormalize(pt_system* sys, const double2* src, double2* dst) {
   const int ne = sys->ne, npw = sys->npw;
-  PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, src, npw, src, npw, kZero, sys->S, ne));
+  PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, src, npw, src, npw, kZero, sys->S, ne,
+                      pt::GEMM_HERM));
   PT_CK(pt::cholesky(sys->S, ne, sys->status, sys->s));
   int h = 0;
   PT_TRY(read_status(sys, &h));
   if (h != 0) { sys->err = "orthonormalisation: overlap matrix is not positive definite"; return PT_ERR_NOT_PD; }
   PT_CK(pt::tri_inverse(sys->S, sys->Linv, ne, sys->s));
-  PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, src, npw, sys->Linv, ne, kZero, dst, npw));
+  PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, src, npw, sys->Linv, ne, kZero, dst, npw,
+                      pt::GEMM_TRI_B));
   return PT_OK;
 }
 
-// exchange data of psi (psi_r current): wg = V_X psi, Mneg = -psi^H wg, ACE
 // ACE data of the current (psi, wg): Mneg = -Psi^H W; Cholesky -M = L L^H;
 // xi = W L^{-H} (ACE construction following Eq. 3 and the ACE definition).
 static pt_status ace_from_w(pt_system* sys) {
   const int ne = sys->ne, npw = sys->npw;
   const bool ace = sys->p.fock_mode == PT_FOCK_ACE && sys->p.alpha != 0.0;
-  if (sys->mixed && ace)
-    PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kMinusOne, sys->psi, npw, sys->wg, npw, kZero, sys->Mneg, ne));
-  else
+  if (sys->mixed && ace) {
+    PT_TRY(to32(sys, sys->psi, sys->ga32, (long)npw * ne));
+    PT_TRY(to32(sys, sys->wg, sys->gb32, (long)npw * ne));
+    PT_TRY(gemm32(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kMinusOne, sys->ga32, npw, sys->gb32, npw, kZero, sys->Mneg, ne));
+  } else
     PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kMinusOne, sys->psi, npw, sys->wg, npw, kZero, sys->Mneg, ne));
   sys->have_ace = false;
   if (!ace) return PT_OK;
@@ -499,14 +529,20 @@ static pt_status ace_from_w(pt_system* sys) {
   PT_TRY(read_status(sys, &h));
   if (h != 0) { sys->err = "ACE: -M is not positive definite"; return PT_ERR_NOT_PD; }
   PT_CK(pt::tri_inverse(sys->S, sys->Linv, ne, sys->s));
-  if (sys->mixed)
-    PT_TRY(gemm<float>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->wg, npw, sys->Linv, ne, kZero, sys->xi, npw));
-  else
-    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->wg, npw, sys->Linv, ne, kZero, sys->xi, npw));
+  if (sys->mixed) {
+    // W is still in gb32; xi and its complex64 copy for the FP32 ACE products
+    PT_TRY(to32(sys, sys->Linv, sys->gs32, (long)ne * ne));
+    PT_TRY(gemm32(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->gb32, npw, sys->gs32, ne, kZero, sys->xi, npw,
+                  pt::GEMM_TRI_B));
+    PT_TRY(to32(sys, sys->xi, sys->xi32, (long)npw * ne));
+  } else
+    PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_H, npw, ne, ne, kOne, sys->wg, npw, sys->Linv, ne, kZero, sys->xi, npw,
+                        pt::GEMM_TRI_B));
   sys->have_ace = true;
   return PT_OK;
 }
 
+// exchange data of psi (psi_r current): wg = V_X psi, then its ACE data
 static pt_status exchange_data(pt_system* sys) {
   PT_TRY(exchange_sym(sys, sys->wg, 0));
   return ace_from_w(sys);
@@ -516,8 +552,10 @@ static pt_status exchange_data(pt_system* sys) {
 static pt_status ace_apply(pt_system* sys, const double2* X, int ncols, double2* out) {
   const int ne = sys->ne, npw = sys->npw;
   if (sys->mixed) {
-    PT_TRY(gemm<float>(sys, pt::OP_H, pt::OP_N, ne, ncols, npw, kOne, sys->xi, npw, X, npw, kZero, sys->Z, ne));
-    PT_TRY(gemm<float>(sys, pt::OP_N, pt::OP_N, npw, ncols, ne, kMinusOne, sys->xi, npw, sys->Z, ne, kOne, out, npw));
+    PT_TRY(to32(sys, X, sys->ga32, (long)npw * ncols));
+    PT_TRY(gemm32(sys, pt::OP_H, pt::OP_N, ne, ncols, npw, kOne, sys->xi32, npw, sys->ga32, npw, kZero, sys->Z, ne));
+    PT_TRY(to32(sys, sys->Z, sys->gs32, (long)ne * ncols));
+    PT_TRY(gemm32(sys, pt::OP_N, pt::OP_N, npw, ncols, ne, kMinusOne, sys->xi32, npw, sys->gs32, ne, kOne, out, npw));
   } else {
     PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ncols, npw, kOne, sys->xi, npw, X, npw, kZero, sys->Z, ne));
     PT_TRY(gemm<double>(sys, pt::OP_N, pt::OP_N, npw, ncols, ne, kMinusOne, sys->xi, npw, sys->Z, ne, kOne, out, npw));

@@ -101,11 +101,19 @@ int fock_build_tiles(int n_occ, int n_x, int tile, int sym, int tiles_per_launch
 // C(M x N) = alpha * op(A) op(B) + beta * C, complex, column-major, batched by strides.
 // A element (i, k) of op(A) == N: A[i + k * lda]; == H: conj(A[k + i * lda]).
 // Inputs stored as complex128; Tc is the compute / accumulate precision.
+// structure: GEMM_HERM for C = A^H A (only the lower half is computed, the upper
+// half is its conjugate mirror); GEMM_TRI_B when op(B) is upper triangular.
 enum { OP_N = 0, OP_H = 1 };
+enum { GEMM_GENERAL = 0, GEMM_HERM = 1, GEMM_TRI_B = 2 };
 template <typename Tc>
 cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const double2* A, long lda, long strideA,
                  const double2* B, long ldb, long strideB, double2 beta, double2* C, long ldc, long strideC,
-                 int batch, double2* splitk_ws, size_t splitk_ws_elems, cudaStream_t s);
+                 int batch, double2* splitk_ws, size_t splitk_ws_elems, cudaStream_t s,
+                 int structure = GEMM_GENERAL);
+// The same product from complex64 copies of A and B, computed in FP32 (C stays complex128).
+cudaError_t gemm_c64(int opA, int opB, int M, int N, int K, double2 alpha, const float2* A, long lda, const float2* B,
+                     long ldb, double2 beta, double2* C, long ldc, double2* splitk_ws, size_t splitk_ws_elems,
+                     cudaStream_t s, int structure = GEMM_GENERAL);
 // In-place lower Cholesky of an n x n Hermitian matrix (column-major, lower
 // triangle used and overwritten, upper set to 0). *d_status = 1 on a
 // non-positive pivot.

@@ -3,9 +3,11 @@
 //   M = Psi^H W, xi^H X, xi Y (ACE), Psi^H Psi and Psi L^{-H} (Sec. 3.4),
 //   Cholesky factorisations (orthonormalisation, -M of ACE) and L^{-1}.
 // GEMM: 64 x 64 output tiles, 256 threads with 4 x 4 complex micro-tiles,
-// operands staged in shared memory in the compute precision; the long
-// reduction over the basis is split over blocks (split-K) into a workspace
-// and summed in a fixed order, so results are deterministic.
+// operands staged in shared memory in the compute precision (double-buffered,
+// next slice prefetched into registers); the long reduction over the basis is
+// split over blocks (split-K) into a workspace and summed in a fixed order, so
+// results are deterministic. Hermitian products (Psi^H Psi) compute half the
+// tiles; products with a triangular factor stop the reduction at the diagonal.
 #include <algorithm>
 #include <cmath>
 
@@ -14,68 +16,117 @@
 
 namespace pt {
 
-constexpr int GBM = 64, GBN = 64, GBK = 8;
+constexpr int GBM = 64, GBN = 64;
+template <typename C> __device__ __forceinline__ C to_compute(double2 v) { return cvt<C>(v); }
+template <typename C> __device__ __forceinline__ C to_compute(float2 v);
+template <> __device__ __forceinline__ float2 to_compute<float2>(float2 v) { return v; }
+template <typename Tc> struct GemmK { static constexpr int V = 16; };
+template <> struct GemmK<double> { static constexpr int V = 8; };
 
-template <typename Tc>
-__global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int M, int N, int K, int kchunk, int ksplit,
-                                              double2 alpha, const double2* __restrict__ A, long lda, long sA,
-                                              const double2* __restrict__ B, long ldb, long sB, double2 beta,
+// Output structure the caller promises (skipped work is exactly zero or implied):
+//   GEMM_HERM   C = A^H A is Hermitian: only tiles on or below the diagonal are
+//               computed; the upper triangle is written as the conjugate mirror.
+//   GEMM_TRI_B  op(B) is upper triangular (op(B)[k][j] = 0 for k > j): the
+//               reduction for output columns [n0, n0 + 64) stops at n0 + 64.
+// One block computes a 64 x 64 tile over its K chunk with 256 threads (4 x 4
+// complex register tiles). The next K slice is fetched into registers while the
+// current one is multiplied from the other of two shared-memory buffers, so
+// there is one barrier per K slice. TI is the storage type of A and B
+// (complex128, or complex64 mirrors for FP32 products: converting FP64 inputs
+// inside the product loop would run every re-read element through the FP64
+// pipe, which on this GPU is as costly as the products themselves).
+template <typename Tc, typename TI>
+__global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int M, int N, int K, int kchunk, int ksplit, int structure,
+                                              double2 alpha, const TI* __restrict__ A, long lda, long sA,
+                                              const TI* __restrict__ B, long ldb, long sB, double2 beta,
                                               double2* __restrict__ Cm, long ldc, long sC,
                                               double2* __restrict__ part) {
   using C = cplx<Tc>;
-  __shared__ C As[GBK][GBM + 1];
-  __shared__ C Bs[GBK][GBN + 1];
+  constexpr int GK = GemmK<Tc>::V;
+  constexpr int PA = GBM * GK / 256;   // A elements per thread per slice
+  constexpr int PB = GBN * GK / 256;
+  __shared__ C As[2][GK][GBM + 1];
+  __shared__ C Bs[2][GK][GBN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+  if (structure == GEMM_HERM && m0 + GBM <= n0) return;   // strictly above the diagonal
   const int bz = blockIdx.z / ksplit, kz = blockIdx.z % ksplit;
-  const double2* Ab = A + (long)bz * sA;
-  const double2* Bb = B + (long)bz * sB;
+  const TI* Ab = A + (long)bz * sA;
+  const TI* Bb = B + (long)bz * sB;
   const int kbeg = kz * kchunk;
-  const int kend = min(K, kbeg + kchunk);
+  int kend = min(K, kbeg + kchunk);
+  if (structure == GEMM_TRI_B) kend = min(kend, n0 + GBN);
   C acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = mk((Tc)0, (Tc)0);
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    // stage A tile: (i in [0,64), k in [0,8)) -> 512 elements, 2 per thread
+  C ra[PA], rb[PB];   // next slice, already in the compute precision
+  auto fetch = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < PA; ++q) {
       const int idx = tid + q * 256;
       int i, k;
-      if (opA == OP_N) { i = idx & 63; k = idx >> 6; }
-      else { k = idx & 7; i = idx >> 3; }
+      if (opA == OP_N) { i = idx % GBM; k = idx / GBM; }
+      else { k = idx % GK; i = idx / GK; }
       const int gi = m0 + i, gk = k0 + k;
-      double2 v = make_double2(0.0, 0.0);
+      TI v{};
       if (gi < M && gk < kend) {
         if (opA == OP_N) v = Ab[gi + (long)gk * lda];
         else { v = Ab[gk + (long)gi * lda]; v.y = -v.y; }
       }
-      As[k][i] = cvt<C>(v);
+      ra[q] = to_compute<C>(v);
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < PB; ++q) {
       const int idx = tid + q * 256;
       int j, k;
-      if (opB == OP_N) { k = idx & 7; j = idx >> 3; }
-      else { j = idx & 63; k = idx >> 6; }
+      if (opB == OP_N) { k = idx % GK; j = idx / GK; }
+      else { j = idx % GBN; k = idx / GBN; }
       const int gj = n0 + j, gk = k0 + k;
-      double2 v = make_double2(0.0, 0.0);
+      TI v{};
       if (gj < N && gk < kend) {
         if (opB == OP_N) v = Bb[gk + (long)gj * ldb];
         else { v = Bb[gj + (long)gk * ldb]; v.y = -v.y; }
       }
-      Bs[k][j] = cvt<C>(v);
+      rb[q] = to_compute<C>(v);
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
 #pragma unroll
-    for (int k = 0; k < GBK; ++k) {
+    for (int q = 0; q < PA; ++q) {
+      const int idx = tid + q * 256;
+      int i, k;
+      if (opA == OP_N) { i = idx % GBM; k = idx / GBM; }
+      else { k = idx % GK; i = idx / GK; }
+      As[buf][k][i] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+      const int idx = tid + q * 256;
+      int j, k;
+      if (opB == OP_N) { k = idx % GK; j = idx / GK; }
+      else { j = idx % GBN; k = idx / GBN; }
+      Bs[buf][k][j] = rb[q];
+    }
+  };
+  int buf = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += GK) {
+    const bool more = k0 + GK < kend;
+    if (more) fetch(k0 + GK);   // in flight during the products below
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
       C av[4], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[k][tx + 16 * a];
+      for (int a = 0; a < 4; ++a) av[a] = As[buf][k][tx + 16 * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][ty + 16 * b];
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][k][ty + 16 * b];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -86,7 +137,9 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int M, int N, in
           acc[a][b].y = fma(av[a].y, bv[b].x, acc[a][b].y);
         }
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -94,37 +147,54 @@ __global__ void __launch_bounds__(256) k_gemm(int opA, int opB, int M, int N, in
     for (int b = 0; b < 4; ++b) {
       const int i = m0 + tx + 16 * a, j = n0 + ty + 16 * b;
       if (i < M && j < N) {
+        if (structure == GEMM_HERM && i < j) continue;   // mirrored from (j, i)
         const double2 v = to_d(acc[a][b]);
         if (ksplit > 1) {
           part[(((long)kz * gridDim.z / ksplit + bz) * N + j) * (long)M + i] = v;
         } else {
-          double2* c = Cm + (long)bz * sC + i + (long)j * ldc;
           double2 r = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
+          double2* c = Cm + (long)bz * sC + i + (long)j * ldc;
           if (beta.x != 0.0 || beta.y != 0.0) {
             const double2 o = *c;
             r.x += beta.x * o.x - beta.y * o.y;
             r.y += beta.x * o.y + beta.y * o.x;
           }
           *c = r;
+          if (structure == GEMM_HERM && i != j) {
+            double2* cm = Cm + (long)bz * sC + j + (long)i * ldc;
+            double2 rm = make_double2(alpha.x * v.x + alpha.y * v.y, alpha.y * v.x - alpha.x * v.y);  // alpha conj(v)
+            if (beta.x != 0.0 || beta.y != 0.0) {
+              const double2 o = *cm;
+              rm.x += beta.x * o.x - beta.y * o.y;
+              rm.y += beta.x * o.y + beta.y * o.x;
+            }
+            *cm = rm;
+          }
         }
       }
     }
 }
 
-__global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, double2 alpha, const double2* __restrict__ part,
-                                double2 beta, double2* __restrict__ Cm, long ldc, long sC) {
+// Sums the split-K partials in a fixed order. For GEMM_HERM the partials exist
+// on and below the diagonal; an entry above it is the conjugate of its mirror.
+__global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, int structure, double2 alpha,
+                                const double2* __restrict__ part, double2 beta, double2* __restrict__ Cm, long ldc,
+                                long sC) {
   const long total = (long)batch * M * N;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
     const int i = (int)(t % M);
     const long rest = t / M;
     const int j = (int)(rest % N);
     const int bz = (int)(rest / N);
+    const bool mirror = structure == GEMM_HERM && i < j;
+    const int pi = mirror ? j : i, pj = mirror ? i : j;
     double2 s = make_double2(0.0, 0.0);
     for (int kz = 0; kz < ksplit; ++kz) {
-      const double2 v = part[(((long)kz * batch + bz) * N + j) * (long)M + i];
+      const double2 v = part[(((long)kz * batch + bz) * N + pj) * (long)M + pi];
       s.x += v.x;
       s.y += v.y;
     }
+    if (mirror) s.y = -s.y;
     double2* c = Cm + (long)bz * sC + i + (long)j * ldc;
     double2 r = make_double2(alpha.x * s.x - alpha.y * s.y, alpha.x * s.y + alpha.y * s.x);
     if (beta.x != 0.0 || beta.y != 0.0) {
@@ -136,39 +206,64 @@ __global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, double2 alp
   }
 }
 
-template <typename Tc>
-cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const double2* A, long lda, long strideA,
-                 const double2* B, long ldb, long strideB, double2 beta, double2* C, long ldc, long strideC, int batch,
-                 double2* ws, size_t ws_elems, cudaStream_t s) {
+template <typename Tc, typename TI>
+static cudaError_t gemm_impl(int opA, int opB, int M, int N, int K, double2 alpha, const TI* A, long lda, long strideA,
+                             const TI* B, long ldb, long strideB, double2 beta, double2* C, long ldc, long strideC,
+                             int batch, double2* ws, size_t ws_elems, cudaStream_t s, int structure) {
+  constexpr int GK = GemmK<Tc>::V;
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (structure == GEMM_HERM && M != N) return cudaErrorInvalidValue;
   const int tm = (M + GBM - 1) / GBM, tn = (N + GBN - 1) / GBN;
-  const long tiles = (long)tm * tn * batch;
+  const long tiles = structure == GEMM_HERM ? (long)tm * (tm + 1) / 2 * batch : (long)tm * tn * batch;
+  // split the reduction so that tiles x ksplit fills the resident block slots once
+  // (a second, mostly empty wave would cost as much as the first)
+  static int slots = 0;
+  if (slots == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm<Tc, TI>, 256, 0);
+    slots = std::max(1, sms * std::max(1, per_sm));
+  }
   int ksplit = 1;
-  if (K > 1024 && tiles < 2 * 152) {
-    ksplit = (int)std::min<long>((2 * 152 + tiles - 1) / tiles, (K + 511) / 512);
-    const size_t need = (size_t)ksplit * batch * M * N;
+  if (K > 1024 && tiles < slots) {
+    ksplit = (int)std::max<long>(1, std::min<long>(slots / tiles, (K + 511) / 512));
     while (ksplit > 1 && (size_t)ksplit * batch * M * N > ws_elems) --ksplit;
-    (void)need;
   }
   int kchunk = (K + ksplit - 1) / ksplit;
-  kchunk = ((kchunk + GBK - 1) / GBK) * GBK;
+  kchunk = ((kchunk + GK - 1) / GK) * GK;
   ksplit = std::max(1, (K + kchunk - 1) / kchunk);
-  if (K == 0) { ksplit = 1; kchunk = GBK; }
+  if (K == 0) { ksplit = 1; kchunk = GK; }
   dim3 grid(tm, tn, (unsigned)(batch * ksplit));
-  k_gemm<Tc><<<grid, 256, 0, s>>>(opA, opB, M, N, K, kchunk, ksplit, alpha, A, lda, strideA, B, ldb, strideB, beta, C,
-                                  ldc, strideC, ws); launched();
+  k_gemm<Tc, TI><<<grid, 256, 0, s>>>(opA, opB, M, N, K, kchunk, ksplit, structure, alpha, A, lda, strideA, B, ldb,
+                                  strideB, beta, C, ldc, strideC, ws); launched();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || ksplit == 1) return e;
   const long total = (long)batch * M * N;
   const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
-  k_splitk_reduce<<<blocks, 256, 0, s>>>(M, N, batch, ksplit, alpha, ws, beta, C, ldc, strideC); launched();
+  k_splitk_reduce<<<blocks, 256, 0, s>>>(M, N, batch, ksplit, structure, alpha, ws, beta, C, ldc, strideC); launched();
   return cudaGetLastError();
 }
 
+template <typename Tc>
+cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const double2* A, long lda, long strideA,
+                 const double2* B, long ldb, long strideB, double2 beta, double2* C, long ldc, long strideC, int batch,
+                 double2* ws, size_t ws_elems, cudaStream_t s, int structure) {
+  return gemm_impl<Tc, double2>(opA, opB, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC,
+                                batch, ws, ws_elems, s, structure);
+}
+
+cudaError_t gemm_c64(int opA, int opB, int M, int N, int K, double2 alpha, const float2* A, long lda, const float2* B,
+                     long ldb, double2 beta, double2* C, long ldc, double2* ws, size_t ws_elems, cudaStream_t s,
+                     int structure) {
+  return gemm_impl<float, float2>(opA, opB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1, ws, ws_elems, s,
+                                  structure);
+}
+
 template cudaError_t gemm<double>(int, int, int, int, int, double2, const double2*, long, long, const double2*, long,
-                                  long, double2, double2*, long, long, int, double2*, size_t, cudaStream_t);
+                                  long, double2, double2*, long, long, int, double2*, size_t, cudaStream_t, int);
 template cudaError_t gemm<float>(int, int, int, int, int, double2, const double2*, long, long, const double2*, long,
-                                 long, double2, double2*, long, long, int, double2*, size_t, cudaStream_t);
+                                 long, double2, double2*, long, long, int, double2*, size_t, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // Cholesky, right-looking, one column per pair of launches (pivot, update).
