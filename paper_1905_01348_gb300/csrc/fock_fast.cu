@@ -140,11 +140,14 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
 // (fused between the last forward and first inverse stage of axis 0), inverse
 // along axis 0 and axis 1, store. Blocks are small so that two or more are
 // resident per SM and one block's barrier waits overlap another's work (this
-// beat a single persistent block per SM fed by bulk-copy prefetch).
+// beat a single persistent block per SM fed by bulk-copy prefetch, and one
+// block of 384 threads without sub-batches).
 template <int L> struct Cfg2;
 template <> struct Cfg2<32> { static constexpr int NT = 128, SUB = 32, MINB = 4; };
 template <> struct Cfg2<64> { static constexpr int NT = 256, SUB = 32, MINB = 3; };
-template <> struct Cfg2<96> { static constexpr int NT = 288, SUB = 48, MINB = 2; };
+// 96: 192 threads balance both radices (48 lines x 12 radix-8 or 8 radix-12
+// butterflies = 3 or 2 per thread) and leave room for 152 registers without spills.
+template <> struct Cfg2<96> { static constexpr int NT = 192, SUB = 48, MINB = 2; };
 template <int L> constexpr size_t smem2() { return sizeof(float2) * (size_t)(L + L * WS<L>); }
 
 template <int L>
