@@ -70,6 +70,11 @@ struct pt_system {
   // complex64 copies for the FP32 products of mixed precision: xi (per step) and two
   // operand staging buffers (n_orb x npw) plus one n_orb x n_orb buffer
   float2 *xi32 = nullptr, *ga32 = nullptr, *gb32 = nullptr, *gs32 = nullptr;
+  // basis-sphere tables of the pruned FP32 transforms (cubic 32/64/96 grids)
+  bool use_sphere = false;
+  pt::SphereTables sph{};
+  int *sph_row_idx = nullptr, *sph_row_kbeg = nullptr, *sph_krow = nullptr, *sph_planes = nullptr;
+  unsigned char *sph_rowlive = nullptr, *sph_planelive = nullptr;
   void *w_r = nullptr, *x_r = nullptr, *scratch = nullptr;
   double2 *S = nullptr, *Mneg = nullptr, *Linv = nullptr, *Z = nullptr, *gemm_ws = nullptr;
   size_t gemm_ws_elems = 0;
@@ -229,6 +234,13 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   t->psi_r = c.take<double2>((size_t)N * ne);
   if (mixed) t->psi_r32 = c.take<float2>((size_t)N * ne);
   if (mixed) {
+    const long L0 = p->n[0], L1 = p->n[1];
+    t->sph_row_idx = c.take<int>(L0 * L1);
+    t->sph_row_kbeg = c.take<int>(L0 * L1 + 1);
+    t->sph_krow = c.take<int>(npw);
+    t->sph_planes = c.take<int>(L0);
+    t->sph_rowlive = c.take<unsigned char>(L0 * L1);
+    t->sph_planelive = c.take<unsigned char>(L0);
     t->xi32 = c.take<float2>(pe);
     t->ga32 = c.take<float2>(pe);
     t->gb32 = c.take<float2>(pe);
@@ -258,8 +270,15 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
 // ---------------------------------------------------------------------------
 // building blocks
 
+static const float2* tw32_for(pt_system* sys, int L) { return sys->tw32 + pt::twiddle_offset(L); }
+
 template <typename T>
 static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst) {
+  if (sizeof(T) == 4 && sys->use_sphere) {
+    PT_CK(pt::sphere_to_real(c, sys->npw, (float2*)dst, ncols, sys->g, sys->sph, sys->basis, 1.0 / std::sqrt(sys->vol),
+                             tw32_for(sys, sys->g.n0), sys->s));
+    return PT_OK;
+  }
   PT_CK(pt::scatter_basis<T>(c, sys->npw, dst, ncols, sys->g, sys->basis, sys->npw, 1.0 / std::sqrt(sys->vol), sys->s));
   PT_CK(pt::fft_rows<T>(dst, dst, ncols, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
   PT_CK(pt::fft_cols<T>(dst, ncols, sys->g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
@@ -271,6 +290,12 @@ static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst
 template <typename T>
 static pt_status to_basis(pt_system* sys, void* src, long ncols, double2* out, int accumulate, const double* kin,
                           const double2* x) {
+  if (sizeof(T) == 4 && sys->use_sphere) {
+    PT_CK(pt::sphere_from_real((const float2*)src, nullptr, (float2*)src, ncols, sys->g, sys->sph, sys->basis,
+                               std::sqrt(sys->vol) / sys->N, kin, x, sys->npw, out, sys->npw, accumulate,
+                               tw32_for(sys, sys->g.n0), sys->s));
+    return PT_OK;
+  }
   PT_CK(pt::fft_rows<T>(src, src, ncols, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
   PT_CK(pt::fft_cols<T>(src, ncols, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
   PT_CK(pt::fft_cols<T>(src, ncols, sys->g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
@@ -463,6 +488,12 @@ static pt_status apply_local_scf(pt_system* sys, const double2* c, double2* out)
   float2* hb = reinterpret_cast<float2*>(sys->hbuf);
   for (int c0 = 0; c0 < sys->ne; c0 += sys->hb) {
     const int cnt = std::min(sys->hb, sys->ne - c0);
+    if (sys->use_sphere) {
+      PT_CK(pt::sphere_from_real(sys->psi_r32 + (long)c0 * sys->N, sys->vloc32, hb, cnt, sys->g, sys->sph, sys->basis,
+                                 std::sqrt(sys->vol) / sys->N, sys->kin, c + (long)c0 * sys->npw, sys->npw,
+                                 out + (long)c0 * sys->npw, sys->npw, 0, tw32_for(sys, sys->g.n0), sys->s));
+      continue;
+    }
     PT_CK(pt::fft_rows<float>(sys->psi_r32 + (long)c0 * sys->N, hb, cnt, sys->g, 0, 1.0, sys->vloc32, sys->tw, sys->s));
     PT_CK(pt::fft_cols<float>(hb, cnt, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
     PT_CK(pt::fft_cols<float>(hb, cnt, sys->g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
@@ -911,6 +942,38 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   }
   if (p->n_atoms > 0)
     PT_CK(cudaMemcpyAsync(sys->d_atoms, sys->atoms.data(), sizeof(double) * 3 * p->n_atoms, cudaMemcpyHostToDevice, s));
+  if (sys->mixed && pt::sphere_fast_supported(sys->g)) {
+    // live rows (i0, i1) of the basis sphere in flat order and the live i0 planes
+    const int L = n0;
+    std::vector<int> row_idx, row_kbeg, krow(npw), planes;
+    std::vector<unsigned char> rowlive((size_t)L * L, 0), planelive(L, 0);
+    int prev = -1;
+    for (int k = 0; k < npw; ++k) {
+      const int row = idx[k] / L;
+      if (row != prev) {
+        row_idx.push_back(row);
+        row_kbeg.push_back(k);
+        rowlive[row] = 1;
+        planelive[row / L] = 1;
+        prev = row;
+      }
+      krow[k] = (int)row_idx.size() - 1;
+    }
+    row_kbeg.push_back(npw);
+    for (int i0 = 0; i0 < L; ++i0)
+      if (planelive[i0]) planes.push_back(i0);
+    PT_CK(cudaMemcpyAsync(sys->sph_row_idx, row_idx.data(), sizeof(int) * row_idx.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaMemcpyAsync(sys->sph_row_kbeg, row_kbeg.data(), sizeof(int) * row_kbeg.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaMemcpyAsync(sys->sph_krow, krow.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
+    if (!planes.empty())
+      PT_CK(cudaMemcpyAsync(sys->sph_planes, planes.data(), sizeof(int) * planes.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaMemcpyAsync(sys->sph_rowlive, rowlive.data(), rowlive.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaMemcpyAsync(sys->sph_planelive, planelive.data(), planelive.size(), cudaMemcpyHostToDevice, s));
+    PT_CK(cudaStreamSynchronize(s));
+    sys->sph = pt::SphereTables{(int)row_idx.size(), sys->sph_row_idx, sys->sph_row_kbeg, sys->sph_krow,
+                                sys->sph_rowlive, (int)planes.size(), sys->sph_planes, sys->sph_planelive};
+    sys->use_sphere = true;
+  }
   sys->tw.d64 = sys->tw64;
   sys->tw.d32 = sys->tw32;
   // pair tiles of the symmetric exchange

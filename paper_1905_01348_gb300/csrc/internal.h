@@ -50,6 +50,31 @@ cudaError_t gather_basis(const void* in, double2* out, long out_ld, long nvol, G
                          cudaStream_t s);
 cudaError_t convert_c128_to_c64(const double2* in, float2* out, long n, cudaStream_t s);
 
+// ---- sphere-pruned FP32 transforms for cubic 32/64/96 grids (fft_sphere.cu) --
+// Device tables of the basis sphere. Live rows are the (i0, i1) with at least
+// one basis vector, in increasing flat order; their basis vectors are the
+// contiguous range [row_kbeg[r], row_kbeg[r + 1]) of the basis listing.
+struct SphereTables {
+  int nrows;
+  const int* row_idx;             // i0 * L + i1 of live row r
+  const int* row_kbeg;            // nrows + 1 entries
+  const int* krow;                // live-row ordinal of basis vector k
+  const unsigned char* rowlive;   // L * L flags, (i0, i1)
+  int nplanes;
+  const int* planes;              // live i0 values
+  const unsigned char* planelive; // L flags
+};
+bool sphere_fast_supported(Grid3 g);
+// vol[v] = sum_k coef[v][k] * scale * exp(+i G_k r) on the grid (complex64 volumes).
+cudaError_t sphere_to_real(const double2* coef, long ldc, float2* vol, long nvol, Grid3 g, const SphereTables& st,
+                           const int* basis, double scale, const float2* tw_L, cudaStream_t s);
+// out[v][k] = scale * F[mul * vol[v]](G_k) (+ kin[k] x[v][k]) (+ out[v][k] if accumulate),
+// F the forward transform; mul may be null; `work` (nvol volumes) may be `vol`.
+cudaError_t sphere_from_real(const float2* vol, const float* mul, float2* work, long nvol, Grid3 g,
+                             const SphereTables& st, const int* basis, double scale, const double* kin,
+                             const double2* x, long ldx, double2* out, long ldo, int accumulate, const float2* tw_L,
+                             cudaStream_t s);
+
 // ---- Fock exchange pair pipeline (fock.cu) ----------------------------------
 constexpr int kTileMax = 4;
 struct PairTile {

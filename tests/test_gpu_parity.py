@@ -151,3 +151,21 @@ def test_apply_h_exact_mixed_cubic(pkg):
     Y = (s.apply_h(Xd, pkg.PT_FOCK_EXACT) - s.apply_h(Xd, pkg.PT_FOCK_NONE)).cpu().numpy().T
     assert rel(Y, ref) < 2e-5
     s.close()
+
+
+def test_ptcn_steps_mixed_si8(pkg):
+    """Mixed-precision PT-CN steps on the 32^3 Si8 cell (FP32 sphere-pruned
+    orbital transforms, local-potential products, pair FFTs and ACE products)
+    against the FP64 oracle: FP32 rounding, amplified by the fixed-point
+    iteration, stays far below the 1e-4 bound; an indexing error would not."""
+    w = syn.si_workload("si8", relax_iters=3, precision="mixed", fock_mode="ace", scf_fixed_iters=4, dt=1.0)
+    model, C0 = make(w, seed=5)
+    st = model.init_state(C0)
+    s = pkg.System(w, C0)
+    assert rel(s.orbitals().T, st.Psi) < 1e-4
+    for _ in range(2):
+        st, info_o = model.step(st)
+        status, info_g = s.step()
+        assert rel(s.orbitals().T, st.Psi) < 1e-4
+        assert abs(info_g["energy"] - info_o.energy) < 1e-6 * abs(info_o.energy)
+    s.close()
