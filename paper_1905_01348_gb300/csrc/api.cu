@@ -63,7 +63,9 @@ struct pt_system {
   double* d_atoms = nullptr;
   float* vloc32 = nullptr;
   double2 *psi = nullptr, *psi_half = nullptr, *psi_f = nullptr, *hpsi = nullptr, *tmp = nullptr, *rbuf = nullptr;
-  double2 *wg = nullptr, *xi = nullptr, *xprev = nullptr, *rprev = nullptr, *dX = nullptr, *dR = nullptr;
+  double2 *wg = nullptr, *xi = nullptr, *xprev = nullptr, *rprev = nullptr;
+  // Anderson history: complex128, or complex64 in mixed precision
+  unsigned char *dX = nullptr, *dR = nullptr;
   double2* hbuf = nullptr;
   double2* psi_r = nullptr;
   float2* psi_r32 = nullptr;
@@ -228,12 +230,13 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   t->xi = c.take<double2>(pe);
   t->xprev = c.take<double2>(pe);
   t->rprev = c.take<double2>(pe);
-  t->dX = c.take<double2>(pe * std::max(1, m));
-  t->dR = c.take<double2>(pe * std::max(1, m));
+  const size_t hs = mixed ? sizeof(float2) : sizeof(double2);
+  t->dX = c.take<unsigned char>(pe * std::max(1, m) * hs);
+  t->dR = c.take<unsigned char>(pe * std::max(1, m) * hs);
   t->hbuf = c.take<double2>((size_t)N * hb);
   t->psi_r = c.take<double2>((size_t)N * ne);
   if (mixed) t->psi_r32 = c.take<float2>((size_t)N * ne);
-  if (mixed) {
+  {
     const long L0 = p->n[0], L1 = p->n[1];
     t->sph_row_idx = c.take<int>(L0 * L1);
     t->sph_row_kbeg = c.take<int>(L0 * L1 + 1);
@@ -241,6 +244,8 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
     t->sph_planes = c.take<int>(L0);
     t->sph_rowlive = c.take<unsigned char>(L0 * L1);
     t->sph_planelive = c.take<unsigned char>(L0);
+  }
+  if (mixed) {
     t->xi32 = c.take<float2>(pe);
     t->ga32 = c.take<float2>(pe);
     t->gb32 = c.take<float2>(pe);
@@ -270,13 +275,14 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
 // ---------------------------------------------------------------------------
 // building blocks
 
-static const float2* tw32_for(pt_system* sys, int L) { return sys->tw32 + pt::twiddle_offset(L); }
+static const float2* tw_for(pt_system* sys, int L, float*) { return sys->tw32 + pt::twiddle_offset(L); }
+static const double2* tw_for(pt_system* sys, int L, double*) { return sys->tw64 + pt::twiddle_offset(L); }
 
 template <typename T>
 static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst) {
-  if (sizeof(T) == 4 && sys->use_sphere) {
-    PT_CK(pt::sphere_to_real(c, sys->npw, (float2*)dst, ncols, sys->g, sys->sph, sys->basis, 1.0 / std::sqrt(sys->vol),
-                             tw32_for(sys, sys->g.n0), sys->s));
+  if (sys->use_sphere) {
+    PT_CK(pt::sphere_to_real(c, sys->npw, (pt::cplx<T>*)dst, ncols, sys->g, sys->sph, sys->basis,
+                             1.0 / std::sqrt(sys->vol), tw_for(sys, sys->g.n0, (T*)nullptr), sys->s));
     return PT_OK;
   }
   PT_CK(pt::scatter_basis<T>(c, sys->npw, dst, ncols, sys->g, sys->basis, sys->npw, 1.0 / std::sqrt(sys->vol), sys->s));
@@ -290,10 +296,10 @@ static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst
 template <typename T>
 static pt_status to_basis(pt_system* sys, void* src, long ncols, double2* out, int accumulate, const double* kin,
                           const double2* x) {
-  if (sizeof(T) == 4 && sys->use_sphere) {
-    PT_CK(pt::sphere_from_real((const float2*)src, nullptr, (float2*)src, ncols, sys->g, sys->sph, sys->basis,
-                               std::sqrt(sys->vol) / sys->N, kin, x, sys->npw, out, sys->npw, accumulate,
-                               tw32_for(sys, sys->g.n0), sys->s));
+  if (sys->use_sphere) {
+    PT_CK(pt::sphere_from_real((const pt::cplx<T>*)src, (const T*)nullptr, (pt::cplx<T>*)src, ncols, sys->g, sys->sph,
+                               sys->basis, std::sqrt(sys->vol) / sys->N, kin, x, sys->npw, out, sys->npw, accumulate,
+                               tw_for(sys, sys->g.n0, (T*)nullptr), sys->s));
     return PT_OK;
   }
   PT_CK(pt::fft_rows<T>(src, src, ncols, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
@@ -344,6 +350,13 @@ static pt_status kerker_mix(pt_system* sys) {
 static pt_status apply_local_from_real(pt_system* sys, const double2* c, double2* out) {
   for (int c0 = 0; c0 < sys->ne; c0 += sys->hb) {
     const int cnt = std::min(sys->hb, sys->ne - c0);
+    if (sys->use_sphere) {
+      PT_CK(pt::sphere_from_real(sys->psi_r + (long)c0 * sys->N, sys->vloc, sys->hbuf, cnt, sys->g, sys->sph,
+                                 sys->basis, std::sqrt(sys->vol) / sys->N, sys->kin, c + (long)c0 * sys->npw, sys->npw,
+                                 out + (long)c0 * sys->npw, sys->npw, 0, tw_for(sys, sys->g.n0, (double*)nullptr),
+                                 sys->s));
+      continue;
+    }
     PT_CK(pt::fft_rows<double>(sys->psi_r + (long)c0 * sys->N, sys->hbuf, cnt, sys->g, 0, 1.0, sys->vloc, sys->tw,
                                sys->s));
     PT_CK(pt::fft_cols<double>(sys->hbuf, cnt, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
@@ -491,7 +504,8 @@ static pt_status apply_local_scf(pt_system* sys, const double2* c, double2* out)
     if (sys->use_sphere) {
       PT_CK(pt::sphere_from_real(sys->psi_r32 + (long)c0 * sys->N, sys->vloc32, hb, cnt, sys->g, sys->sph, sys->basis,
                                  std::sqrt(sys->vol) / sys->N, sys->kin, c + (long)c0 * sys->npw, sys->npw,
-                                 out + (long)c0 * sys->npw, sys->npw, 0, tw32_for(sys, sys->g.n0), sys->s));
+                                 out + (long)c0 * sys->npw, sys->npw, 0, tw_for(sys, sys->g.n0, (float*)nullptr),
+                                 sys->s));
       continue;
     }
     PT_CK(pt::fft_rows<float>(sys->psi_r32 + (long)c0 * sys->N, hb, cnt, sys->g, 0, 1.0, sys->vloc32, sys->tw, sys->s));
@@ -693,9 +707,11 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
       }
       sys->and_order.push_back(newslot);
     }
+    const size_t hs = sys->mixed ? sizeof(float2) : sizeof(double2);
     PT_CK(pt::anderson_push(sys->psi_f, sys->rbuf, sys->xprev, sys->rprev,
-                            sys->dX + (newslot >= 0 ? newslot : 0) * stride,
-                            sys->dR + (newslot >= 0 ? newslot : 0) * stride, n, newslot >= 0 ? 1 : 0, sys->s));
+                            sys->dX + (newslot >= 0 ? newslot : 0) * stride * hs,
+                            sys->dR + (newslot >= 0 ? newslot : 0) * stride * hs, n, newslot >= 0 ? 1 : 0,
+                            sys->mixed ? 1 : 0, sys->s));
     have_prev = true;
     pt::SlotList sl{};
     sl.k = (int)sys->and_order.size();
@@ -706,7 +722,7 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
       PT_CK(pt::anderson_solve(sys->gram, sys->rhs, sl, m, ne, sys->gamma, sys->s));
     }
     PT_CK(pt::anderson_update(sys->psi_f, sys->rbuf, sys->dX, sys->dR, stride, sl, sys->gamma, std::max(m, 1), npw, n,
-                              sys->p.anderson_beta, sys->s));
+                              sys->p.anderson_beta, sys->mixed ? 1 : 0, sys->s));
     // new density and its change
     PT_TRY(real_orbitals_scf(sys, sys->psi_f));
     PT_TRY(density_scf(sys, sys->rho2));
@@ -942,7 +958,7 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   }
   if (p->n_atoms > 0)
     PT_CK(cudaMemcpyAsync(sys->d_atoms, sys->atoms.data(), sizeof(double) * 3 * p->n_atoms, cudaMemcpyHostToDevice, s));
-  if (sys->mixed && pt::sphere_fast_supported(sys->g)) {
+  if (pt::sphere_fast_supported(sys->g)) {
     // live rows (i0, i1) of the basis sphere in flat order and the live i0 planes
     const int L = n0;
     std::vector<int> row_idx, row_kbeg, krow(npw), planes;

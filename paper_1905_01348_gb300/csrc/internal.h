@@ -65,14 +65,20 @@ struct SphereTables {
   const unsigned char* planelive; // L flags
 };
 bool sphere_fast_supported(Grid3 g);
-// vol[v] = sum_k coef[v][k] * scale * exp(+i G_k r) on the grid (complex64 volumes).
+// vol[v] = sum_k coef[v][k] * scale * exp(+i G_k r) on the grid (complex64 or complex128 volumes).
 cudaError_t sphere_to_real(const double2* coef, long ldc, float2* vol, long nvol, Grid3 g, const SphereTables& st,
                            const int* basis, double scale, const float2* tw_L, cudaStream_t s);
+cudaError_t sphere_to_real(const double2* coef, long ldc, double2* vol, long nvol, Grid3 g, const SphereTables& st,
+                           const int* basis, double scale, const double2* tw_L, cudaStream_t s);
 // out[v][k] = scale * F[mul * vol[v]](G_k) (+ kin[k] x[v][k]) (+ out[v][k] if accumulate),
 // F the forward transform; mul may be null; `work` (nvol volumes) may be `vol`.
 cudaError_t sphere_from_real(const float2* vol, const float* mul, float2* work, long nvol, Grid3 g,
                              const SphereTables& st, const int* basis, double scale, const double* kin,
                              const double2* x, long ldx, double2* out, long ldo, int accumulate, const float2* tw_L,
+                             cudaStream_t s);
+cudaError_t sphere_from_real(const double2* vol, const double* mul, double2* work, long nvol, Grid3 g,
+                             const SphereTables& st, const int* basis, double scale, const double* kin,
+                             const double2* x, long ldx, double2* out, long ldo, int accumulate, const double2* tw_L,
                              cudaStream_t s);
 
 // ---- Fock exchange pair pipeline (fock.cu) ----------------------------------

@@ -225,24 +225,32 @@ cudaError_t precond_step(double2* x, const double2* R, const double* kin, int np
 
 // ---- Anderson mixing (Sec. 3.4), per band -------------------------------------------
 // push: dX[slot] = x - x_prev, dR[slot] = r - r_prev (when have_prev), then x_prev = x, r_prev = r
+// History entries are stored as H: complex128, or complex64 in mixed precision
+// (the differences of successive iterates and residuals, whose rounding to FP32
+// only perturbs the least-squares extrapolation, not the fixed point).
+template <typename H>
 __global__ void k_anderson_push(const double2* __restrict__ x, const double2* __restrict__ r, double2* __restrict__ xp,
-                                double2* __restrict__ rp, double2* __restrict__ dx, double2* __restrict__ dr, long n,
+                                double2* __restrict__ rp, H* __restrict__ dx, H* __restrict__ dr, long n,
                                 int have_prev) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     const double2 a = x[t], b = r[t];
     if (have_prev) {
       const double2 c = xp[t], d = rp[t];
-      dx[t] = make_double2(a.x - c.x, a.y - c.y);
-      dr[t] = make_double2(b.x - d.x, b.y - d.y);
+      dx[t] = {(decltype(H::x))(a.x - c.x), (decltype(H::x))(a.y - c.y)};
+      dr[t] = {(decltype(H::x))(b.x - d.x), (decltype(H::x))(b.y - d.y)};
     }
     xp[t] = a;
     rp[t] = b;
   }
 }
 
-cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, double2* dx, double2* dr,
-                          long n, int have_prev, cudaStream_t s) {
-  k_anderson_push<<<nblk(n, 256), 256, 0, s>>>(x, r, xp, rp, dx, dr, n, have_prev); launched();
+cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, void* dx, void* dr, long n,
+                          int have_prev, int f32, cudaStream_t s) {
+  if (f32)
+    k_anderson_push<float2><<<nblk(n, 256), 256, 0, s>>>(x, r, xp, rp, (float2*)dx, (float2*)dr, n, have_prev);
+  else
+    k_anderson_push<double2><<<nblk(n, 256), 256, 0, s>>>(x, r, xp, rp, (double2*)dx, (double2*)dr, n, have_prev);
+  launched();
   return cudaGetLastError();
 }
 
@@ -250,19 +258,19 @@ cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, doubl
 // conjugate at [new][slot_q]) and rhs[b][q] = <dR_{slot_q}, r>_b for the
 // history slots in order (oldest first). One block per band; the slots are
 // processed four at a time to bound registers.
-// F32 (mixed precision): the products are formed in FP32 from FP32 copies of
-// the FP64 vectors and summed in FP32 over each thread's share of the basis
-// (about npw / 256 terms); the per-thread sums are reduced in FP64. FP64
-// otherwise. The Gram matrix and right-hand side feed the FP64 solve either way.
-template <bool F32>
-__global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride, SlotList sl, int newslot,
+// Complex64 history (mixed precision): the products are formed in FP32 and
+// summed in FP32 over each thread's share of the basis (about npw / 256 terms);
+// the per-thread sums are reduced in FP64. FP64 otherwise. The Gram matrix and
+// right-hand side feed the FP64 solve either way.
+template <typename H>
+__global__ void k_anderson_dots(const H* __restrict__ dR, long slot_stride, SlotList sl, int newslot,
                                 const double2* __restrict__ r, int npw, int mdim, double2* __restrict__ gram,
                                 double2* __restrict__ rhs) {
-  using A = typename std::conditional<F32, float, double>::type;
+  using A = decltype(H::x);
   const int b = blockIdx.x;
   const int k = sl.k;
   const long boff = (long)b * npw;
-  const double2* dn = dR + (long)newslot * slot_stride + boff;
+  const H* dn = dR + (long)newslot * slot_stride + boff;
   const double2* rb = r + boff;
   __shared__ double sh[16][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -271,13 +279,14 @@ __global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = (A)0;
     for (int g = threadIdx.x; g < npw; g += blockDim.x) {
-      const double2 vnd = dn[g], vrd = rb[g];
-      const A vnx = (A)vnd.x, vny = (A)vnd.y, vrx = (A)vrd.x, vry = (A)vrd.y;
+      const H vnd = dn[g];
+      const double2 vrd = rb[g];
+      const A vnx = vnd.x, vny = vnd.y, vrx = (A)vrd.x, vry = (A)vrd.y;
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) {
         if (q0 + qq < k) {
-          const double2 ud = dR[(long)sl.s[q0 + qq] * slot_stride + boff + g];
-          const A ux = (A)ud.x, uy = (A)ud.y;
+          const H ud = dR[(long)sl.s[q0 + qq] * slot_stride + boff + g];
+          const A ux = ud.x, uy = ud.y;
           acc[4 * qq + 0] += ux * vnx + uy * vny;
           acc[4 * qq + 1] += ux * vny - uy * vnx;
           acc[4 * qq + 2] += ux * vrx + uy * vry;
@@ -314,11 +323,13 @@ __global__ void k_anderson_dots(const double2* __restrict__ dR, long slot_stride
   }
 }
 
-cudaError_t anderson_dots(const double2* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
+cudaError_t anderson_dots(const void* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
                           int npw, int ne, int mdim, double2* gram, double2* rhs, int f32, cudaStream_t s) {
   if (sl.k > kSlotMax) return cudaErrorInvalidValue;
-  if (f32) k_anderson_dots<true><<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
-  else k_anderson_dots<false><<<ne, 256, 0, s>>>(dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
+  if (f32)
+    k_anderson_dots<float2><<<ne, 256, 0, s>>>((const float2*)dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
+  else
+    k_anderson_dots<double2><<<ne, 256, 0, s>>>((const double2*)dR, slot_stride, sl, newslot, r, npw, mdim, gram, rhs);
   launched();
   return cudaGetLastError();
 }
@@ -385,33 +396,58 @@ cudaError_t anderson_solve(const double2* gram, const double2* rhs, const SlotLi
 }
 
 // x <- x + beta r - sum_q (dX_q + beta dR_q) gamma_q  (per band)
-__global__ void k_anderson_update(double2* __restrict__ x, const double2* __restrict__ r,
-                                  const double2* __restrict__ dX, const double2* __restrict__ dR, long slot_stride,
-                                  SlotList sl, const double2* __restrict__ gamma, int mdim, int npw, long n,
-                                  double beta) {
+// x += beta r - sum_q gamma_q (dX_q + beta dR_q). One block row per band (no
+// division per element). With complex64 history the correction sum is formed
+// in FP32 and added to the FP64 iterate once.
+template <typename H>
+__global__ void k_anderson_update(double2* __restrict__ x, const double2* __restrict__ r, const H* __restrict__ dX,
+                                  const H* __restrict__ dR, long slot_stride, SlotList sl,
+                                  const double2* __restrict__ gamma, int mdim, int npw, double beta) {
+  using A = decltype(H::x);
   const int k = sl.k;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-    const long b = t / npw;
+  const int b = blockIdx.y;
+  const long boff = (long)b * npw;
+  __shared__ A gs[2 * kSlotMax];
+  if (threadIdx.x < k) {
+    const double2 g = gamma[(long)b * mdim + threadIdx.x];
+    gs[2 * threadIdx.x] = (A)g.x;
+    gs[2 * threadIdx.x + 1] = (A)g.y;
+  }
+  __syncthreads();
+  const A bt = (A)beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npw; i += gridDim.x * blockDim.x) {
+    const long t = boff + i;
+    A cx = 0, cy = 0;
+    for (int q = 0; q < k; ++q) {
+      const long sq = (long)sl.s[q] * slot_stride + t;
+      const H a = dX[sq], c = dR[sq];
+      const A ux = a.x + bt * c.x, uy = a.y + bt * c.y;
+      const A gx = gs[2 * q], gy = gs[2 * q + 1];
+      cx += ux * gx - uy * gy;
+      cy += ux * gy + uy * gx;
+    }
     double2 v = x[t];
     const double2 rr = r[t];
-    v.x += beta * rr.x;
-    v.y += beta * rr.y;
-    for (int q = 0; q < k; ++q) {
-      const double2 g = gamma[b * mdim + q];
-      const double2 a = dX[(long)sl.s[q] * slot_stride + t];
-      const double2 c = dR[(long)sl.s[q] * slot_stride + t];
-      const double2 u = make_double2(a.x + beta * c.x, a.y + beta * c.y);
-      v.x -= u.x * g.x - u.y * g.y;
-      v.y -= u.x * g.y + u.y * g.x;
-    }
+    v.x += beta * rr.x - (double)cx;
+    v.y += beta * rr.y - (double)cy;
     x[t] = v;
   }
 }
 
-cudaError_t anderson_update(double2* x, const double2* r, const double2* dX, const double2* dR, long slot_stride,
-                            const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta,
+cudaError_t anderson_update(double2* x, const double2* r, const void* dX, const void* dR, long slot_stride,
+                            const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta, int f32,
                             cudaStream_t s) {
-  k_anderson_update<<<nblk(n, 256), 256, 0, s>>>(x, r, dX, dR, slot_stride, sl, gamma, mdim, npw, n, beta); launched();
+  if (sl.k > kSlotMax) return cudaErrorInvalidValue;
+  const int ne = npw > 0 ? (int)(n / npw) : 0;
+  if (ne == 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min(32, (npw + 255) / 256), (unsigned)ne);
+  if (f32)
+    k_anderson_update<float2><<<grid, 256, 0, s>>>(x, r, (const float2*)dX, (const float2*)dR, slot_stride, sl, gamma,
+                                                   mdim, npw, beta);
+  else
+    k_anderson_update<double2><<<grid, 256, 0, s>>>(x, r, (const double2*)dX, (const double2*)dR, slot_stride, sl,
+                                                    gamma, mdim, npw, beta);
+  launched();
   return cudaGetLastError();
 }
 

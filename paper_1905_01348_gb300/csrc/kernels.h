@@ -25,15 +25,14 @@ cudaError_t half_step(const double2* psi, const double2* R, double hdt, double2*
 cudaError_t pt_residual(const double2* psi_f, const double2* T, const double2* ph, double hdt, double2* r, long n,
                         double* part, double* out_norm2, cudaStream_t s);
 cudaError_t precond_step(double2* x, const double2* R, const double* kin, int npw, long n, double tau, cudaStream_t s);
-cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, double2* dx, double2* dr,
-                          long n, int have_prev, cudaStream_t s);
-cudaError_t anderson_dots(const double2* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
-                          int npw, int ne, int mdim, double2* gram, double2* rhs, int f32,
-                          cudaStream_t s);
+cudaError_t anderson_push(const double2* x, const double2* r, double2* xp, double2* rp, void* dx, void* dr, long n,
+                          int have_prev, int f32, cudaStream_t s);
+cudaError_t anderson_dots(const void* dR, long slot_stride, const SlotList& sl, int newslot, const double2* r,
+                          int npw, int ne, int mdim, double2* gram, double2* rhs, int f32, cudaStream_t s);
 cudaError_t anderson_solve(const double2* gram, const double2* rhs, const SlotList& sl, int mdim, int ne,
                            double2* gamma, cudaStream_t s);
-cudaError_t anderson_update(double2* x, const double2* r, const double2* dX, const double2* dR, long slot_stride,
-                            const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta,
+cudaError_t anderson_update(double2* x, const double2* r, const void* dX, const void* dR, long slot_stride,
+                            const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta, int f32,
                             cudaStream_t s);
 cudaError_t rho_change(const double* a, const double* b, long N, double* part, double* out, cudaStream_t s);
 // out8: [0] sum vion rho, [1] sum vh rho, [2] sum rho^{4/3}, [3..5] sum r rho,
