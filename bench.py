@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample-s", type=float, default=8.0,
+                    help="host seconds of oracle work per reference-arm step")
     return ap.parse_args()
 
 
@@ -56,6 +58,31 @@ def dist_env():
 
 def pairs_per_exchange(n_orb: int) -> int:
     return n_orb * (n_orb + 1) // 2
+
+
+def workload_config(workload: str, precision: str, world: int) -> dict:
+    """The `config` object of the JSON line (both arms report the same one)."""
+    import synthetic as syn
+    w = syn.si_workload(workload, precision=precision, fock_mode="ace")
+    return {"workload": workload, "grid": list(w["n"]), "n_orb": w["n_orb"],
+            "pairs_per_step": pairs_per_exchange(w["n_orb"]), "fock_mode": "ace", "precision": precision,
+            "scf_tol": w["scf_tol"], "dt_au": w["dt"],
+            "l2": "inputs larger than L2 (orbitals and pair intermediates are GBs)",
+            "parallelism": f"replicas x{world}"}
+
+
+def reduce_max(x: float, device) -> float:
+    """Max of a per-rank float over the process group (the timing rule: slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, t_max_s: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / t_max_s
 
 
 def measured_peaks() -> dict:
@@ -200,7 +227,7 @@ def run_reference(args):
         return 0
     res = []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_pairs_per_s(args.workload, budget_s=8.0, seed=k)
+        r = cpu_oracle_pairs_per_s(args.workload, budget_s=args.ref_sample_s, seed=k)
         if k >= args.warmup:
             res.append(r)
     value = statistics.mean(r["value"] for r in res)
@@ -209,7 +236,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "note": "each step is a bounded sample of the exchange pair loop"},
+            "config": workload_config(args.workload, args.precision, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res[0]["cores"], "kind": "oracle",
                              "sample": res[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -281,12 +308,8 @@ def run_gpu(args):
         return step_ms[min(len(step_ms) - 1, max(0, math.ceil(q * len(step_ms)) - 1))]
     pair_ms, pair_count, groups = pkg.pt_get_timing(sysg.handle, reset=True)
     if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    total_pairs = pairs * args.steps * ws
-    value = total_pairs / (t_ms / 1e3)
+        t_ms = reduce_max(t_ms, dev)
+    value = job_value(pairs * args.steps, ws, t_ms / 1e3)
     ms_per_step = t_ms / args.steps
 
     # roofline of the pair pipeline (F1 + F2 + F3 of every launch group)
@@ -327,11 +350,8 @@ def run_gpu(args):
         barrier()
         te = time.perf_counter() - t0
         if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([te], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": pairs * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            te = reduce_max(te, dev)
+        e2e = {"value": job_value(pairs * args.steps, ws, te), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes,
                "note": "per step: pt_set_state from pinned host memory (orbitals and their exchange; rebuilds ACE "
                        "and observables), pt_cn_step, pt_get_state back to the host buffers"}
@@ -347,11 +367,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded random orbitals, relaxed; Gaussian-well Si supercell)",
-            "config": {"workload": args.workload, "grid": list(w["n"]), "n_orb": n_orb,
-                       "pairs_per_step": pairs, "fock_mode": "ace", "precision": args.precision,
-                       "scf_tol": w["scf_tol"], "dt_au": w["dt"],
-                       "l2": "inputs larger than L2 (orbitals and pair intermediates are GBs)",
-                       "parallelism": f"replicas x{ws}"},
+            "config": workload_config(args.workload, args.precision, ws),
             "wall_s_per_fs": ms_per_step * STEPS_PER_FS / 1e3,
             "step_latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "n": len(step_ms)},
             "scf_iters": [i["scf_iters"] for i in infos],
