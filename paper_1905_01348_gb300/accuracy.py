@@ -1,0 +1,82 @@
+"""Mixed precision against the FP64 path over a trajectory.
+
+Runs the same workload through the C ABI from the same seeded start orbitals
+three times for `--steps` PT-CN steps: FP64 and mixed precision (FP32 pair
+FFTs, ACE and projection products, SCF transforms) at the workload's SCF
+tolerance, and FP64 at a tight tolerance (`--tight-tol`) as the reference.
+The SCF tolerance bounds how far any run may sit from the exact fixed point,
+so the mixed run's error is reported beside the FP64 run's own error at the
+same tolerance. Per step: total-energy difference per atom and dipole
+difference (max over the three components); at the end the subspace defect
+n_orb - ||Psi_a^H Psi_b||_F^2 (zero when the occupied subspaces agree).
+The start state (orthonormalisation and relaxation) is computed by each run
+itself. Prints one JSON object.
+
+    python -m paper_1905_01348_gb300.accuracy --workload si8 --steps 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", default="si8", choices=["si8", "si64", "si216"])
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--fock-mode", default="ace", choices=["ace", "exact"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tight-tol", type=float, default=1e-9)
+    args = ap.parse_args(argv)
+
+    import numpy as np
+    import synthetic as syn
+    from . import _native as nat
+    from . import System, make_params
+
+    nat.load()
+    base = syn.si_workload(args.workload, fock_mode=args.fock_mode)
+    n_atoms = len(base["atoms"])
+    p = make_params(base)
+    g2 = syn.basis_g2(nat.pt_basis_indices(p), base["n"], base["cell"])
+    C0 = syn.initial_coefficients(g2, base["n_orb"], seed=args.seed)
+    runs = {}
+    for name, prec, tol in (("fp64", "fp64", base["scf_tol"]), ("mixed", "mixed", base["scf_tol"]),
+                            ("fp64_tight", "fp64", args.tight_tol)):
+        s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200), C0)
+        e0, d0 = s.observables()
+        rec = {"energy": [e0], "dipole": [np.asarray(d0)], "scf": [], "ms": []}
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            st, info = s.step()
+            rec["ms"].append((time.perf_counter() - t0) * 1e3)
+            rec["energy"].append(info["energy"])
+            rec["dipole"].append(np.asarray(info["dipole"]))
+            rec["scf"].append(info["scf_iters"])
+        rec["psi"] = s.orbitals()
+        s.close()
+        runs[name] = rec
+
+    def compare(a, b):
+        de = [abs(x - y) / n_atoms for x, y in zip(a["energy"], b["energy"])]
+        dd = [float(np.max(np.abs(x - y))) for x, y in zip(a["dipole"], b["dipole"])]
+        ov = a["psi"].conj() @ b["psi"].T
+        return {"max_energy_diff_ha_per_atom": max(de), "max_dipole_diff_au": max(dd),
+                "subspace_defect": float(base["n_orb"] - np.sum(np.abs(ov) ** 2)),
+                "per_step_energy_diff": de, "per_step_dipole_diff": dd}
+
+    ref = runs["fp64_tight"]
+    out = {"workload": args.workload, "steps": args.steps, "fock_mode": args.fock_mode,
+           "scf_tol": base["scf_tol"], "tight_tol": args.tight_tol,
+           "mixed_vs_fp64": compare(runs["mixed"], runs["fp64"]),
+           "mixed_vs_fp64_tight": compare(runs["mixed"], ref),
+           "fp64_vs_fp64_tight": compare(runs["fp64"], ref),
+           "energy_drift_ha_per_atom": {k: abs(r["energy"][-1] - r["energy"][0]) / n_atoms for k, r in runs.items()},
+           "scf_iters": {k: r["scf"] for k, r in runs.items()},
+           "ms_per_step": {k: float(np.median(r["ms"])) for k, r in runs.items()}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
