@@ -8,7 +8,8 @@ reproducible without their data files; the test cells use these stand-ins):
 * V_ext: a periodic sum of Gaussian wells -D exp(-|r - R_a|^2 / (2 sigma^2)),
   defined by its Fourier series
   Vhat(G) = -D (2 pi sigma^2)^{3/2} / Omega * sum_a exp(-i G.R_a) exp(-sigma^2 |G|^2 / 2).
-* External field: a velocity-gauge kick kappa, so the kinetic term is
+* External field: a velocity-gauge kick kappa (plus, when switched on, the
+  laser vector potential A(t) of the PT-CN model), so the kinetic term is
   |G + kappa|^2 / 2 on each basis vector (the phases of the length-gauge
   kick exp(i kappa.r) are not periodic on the cell).
 * V_Hxc: Hartree 4 pi rhohat(G)/|G|^2 with the G = 0 term removed
@@ -82,6 +83,7 @@ class LocalModel:
 
     def __init__(self, grid: Grid, atoms_frac, depth, sigma, kick, alpha, use_hartree=True, use_lda=True):
         self.grid = grid
+        self.kick = np.asarray(kick, dtype=np.float64)
         self.kin = kinetic_diagonal(grid, kick)
         self.v_ion = ion_potential(grid, atoms_frac, depth, sigma)
         self.alpha = float(alpha)
@@ -96,14 +98,20 @@ class LocalModel:
             v = v + (1.0 - self.alpha) * lda_exchange_potential(rho)
         return v
 
-    def apply_local(self, vloc: np.ndarray, X: np.ndarray) -> np.ndarray:
-        """Kinetic + local part of H on the columns of X (npw, m)."""
-        g = self.grid
-        return self.kin[:, None] * X + g.to_basis(vloc[None] * g.to_real(X.T)).T
+    def kin_at(self, a_field) -> np.ndarray:
+        """Kinetic diagonal |G + kappa + A|^2 / 2 for a vector potential A (velocity gauge)."""
+        return kinetic_diagonal(self.grid, self.kick + np.asarray(a_field, dtype=np.float64))
 
-    def energy_terms(self, C: np.ndarray, rho: np.ndarray, exx: float) -> dict:
+    def apply_local(self, vloc: np.ndarray, X: np.ndarray, kin=None) -> np.ndarray:
+        """Kinetic + local part of H on the columns of X (npw, m); kin defaults to the kick's."""
         g = self.grid
-        e = dict(kinetic=float(2.0 * np.sum(self.kin[:, None] * np.abs(C) ** 2)),
+        k = self.kin if kin is None else kin
+        return k[:, None] * X + g.to_basis(vloc[None] * g.to_real(X.T)).T
+
+    def energy_terms(self, C: np.ndarray, rho: np.ndarray, exx: float, kin=None) -> dict:
+        g = self.grid
+        k = self.kin if kin is None else kin
+        e = dict(kinetic=float(2.0 * np.sum(k[:, None] * np.abs(C) ** 2)),
                  ion=float(g.dV * np.sum(self.v_ion * rho)),
                  hartree=0.0, xc=0.0, fock=float(exx))
         if self.use_hartree:

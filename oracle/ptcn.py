@@ -36,6 +36,13 @@ Readings (the paper is silent on these details):
 * The exchange data of Psi_{n+1} (W = V_X Psi_{n+1}, and the ACE operator) are
   produced at the end of a step, where they also give the energy E_{n+1}, and
   the next step reuses them for R_n.
+* Laser (Sec. 4 drives the system with a 380 nm pulse over 30 fs; the pulse
+  shape is shown only in a figure): velocity gauge with the uniform vector
+  potential A(t) = A0 sin^2(pi t / T) sin(omega t) e for 0 <= t <= T and 0
+  after, omega = 2 pi c / 380 nm = 0.1199 a.u., T = 30 fs = 1240.4 a.u.; the
+  kinetic term is |G + kappa + A(t)|^2 / 2. Step n runs from t_n = n dt to
+  t_{n+1}: H_n uses A(t_n), H_f and the observables of Psi_{n+1} use A(t_{n+1}).
+  A0 = 0 (the default) leaves the kick alone.
 * Start state: the paper propagates from a ground state (Sec. 4: the laser
   drives a converged system). The synthetic orbitals are random, and from a
   random start the fixed point of Alg. 1 does not converge at dt = 50 as. So
@@ -87,6 +94,10 @@ class Params:
     relax_tau: float = 1.0
     relax_mix: float = 0.5
     relax_q0: float = 1.0
+    laser_amp: float = 0.0            # A0 (a.u.); 0 switches the laser off
+    laser_omega: float = 0.1199       # carrier frequency (a.u.): 380 nm
+    laser_duration: float = 1240.4    # pulse length T (a.u.): 30 fs
+    laser_dir: tuple = (1.0, 0.0, 0.0)
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -123,6 +134,19 @@ class Model:
                                    p.use_hartree, p.use_lda)
         self.khat = ex.screened_kernel(self.grid, p.omega)
 
+    # -- external field ---------------------------------------------------------
+    def laser(self, t: float) -> np.ndarray:
+        """Laser vector potential A(t) (laser reading in the module header)."""
+        p = self.p
+        if p.laser_amp == 0.0 or t < 0.0 or t > p.laser_duration:
+            return np.zeros(3)
+        env = np.sin(np.pi * t / p.laser_duration) ** 2
+        e = np.asarray(p.laser_dir, dtype=np.float64)
+        return p.laser_amp * env * np.sin(p.laser_omega * t) * e
+
+    def kin_at_step(self, n: int) -> np.ndarray:
+        return self.local.kin_at(self.laser(n * self.p.dt))
+
     # -- pieces of H --------------------------------------------------------
     def density(self, C: np.ndarray) -> np.ndarray:
         return hm.density(self.grid, self.grid.to_real(C.T))
@@ -143,19 +167,19 @@ class Model:
         W = self.vx(C, C)
         return W, C.conj().T @ W, None
 
-    def apply_h(self, C: np.ndarray, X: np.ndarray, fock: str, xi=None) -> np.ndarray:
+    def apply_h(self, C: np.ndarray, X: np.ndarray, fock: str, xi=None, kin=None) -> np.ndarray:
         """H[P] X with P from the columns of C; fock = "exact" | "ace" | "none"."""
         rho = self.density(C)
-        out = self.local.apply_local(self.local.local_potential(rho), X)
+        out = self.local.apply_local(self.local.local_potential(rho), X, kin)
         if fock == "exact":
             out = out + self.vx(C, X)
         elif fock == "ace" and xi is not None:
             out = out + ex.apply_ace(xi, X)
         return out
 
-    def observables(self, C: np.ndarray, M: np.ndarray):
+    def observables(self, C: np.ndarray, M: np.ndarray, kin=None):
         rho = self.density(C)
-        e = self.local.energy_terms(C, rho, float(np.real(np.trace(M))))
+        e = self.local.energy_terms(C, rho, float(np.real(np.trace(M))), kin)
         return e["total"], hm.dipole(self.grid, rho)
 
     # -- state ----------------------------------------------------------------
@@ -190,10 +214,14 @@ class Model:
         ne = st.Psi.shape[1]
         n_el = 2.0 * ne
 
+        # kinetic diagonals of H_n (t_n) and H_{n+1} (t_{n+1})
+        kin_n = self.kin_at_step(st.step)
+        kin_f = self.kin_at_step(st.step + 1)
+
         # Alg. 1: initial residual and half step (H_n Psi_n uses the stored W = V_X[Psi_n] Psi_n)
         Psi_n = st.Psi
         rho_n = self.density(Psi_n)
-        HPsi_n = self.local.apply_local(self.local.local_potential(rho_n), Psi_n) + st.W
+        HPsi_n = self.local.apply_local(self.local.local_potential(rho_n), Psi_n, kin_n) + st.W
         S_n = Psi_n.conj().T @ HPsi_n
         R_n = HPsi_n - Psi_n @ S_n
         Psi_half = Psi_n - 0.5j * dt * R_n
@@ -212,7 +240,7 @@ class Model:
         for it in range(1, n_iter + 1):
             # update the potential and H_f
             vloc = self.local.local_potential(rho_f)
-            HPf = self.local.apply_local(vloc, Psi_f)
+            HPf = self.local.apply_local(vloc, Psi_f, kin_f)
             if p.alpha != 0.0:
                 if p.fock_mode == "exact":
                     HPf = HPf + self.vx(Psi_f, Psi_f)
@@ -237,7 +265,7 @@ class Model:
         # orthonormalise, then the exchange data and observables of Psi_{n+1}
         Psi_next = orthonormalize(Psi_f)
         W, M, xi = self.exchange_data(Psi_next)
-        E, d = self.observables(Psi_next, M)
+        E, d = self.observables(Psi_next, M, kin_f)
         new = State(Psi=Psi_next, W=W, M=M, xi=xi, energy=E, dipole=d, step=st.step + 1)
         return new, StepInfo(scf_iters=it, converged=converged, resid_norm=resid, drho=drho, energy=E, dipole=d)
 

@@ -9,6 +9,11 @@
   iteration where the latter converges (small dt, full nonlinear H).
 * The step output is orthonormal; the Cholesky helper agrees with LAPACK and
   refuses an indefinite matrix.
+* Laser (velocity gauge): the vector potential's closed form; free electrons
+  (single planewaves, no potential) stay fixed and their energy follows
+  2 sum |G + kappa + A(t_n)|^2 / 2 exactly; with wells and the field the
+  density matrix converges at second order to a fine midpoint-exponential
+  reference of the time-dependent linear H.
 """
 import numpy as np
 import pytest
@@ -100,3 +105,71 @@ def test_cholesky_helper():
     L = pc.cholesky_or_none(S)
     assert np.max(np.abs(L - np.linalg.cholesky(S))) < 1e-13
     assert pc.cholesky_or_none(S - 100 * np.eye(5)) is None
+
+
+# ---- laser field (velocity gauge, time-dependent kinetic term) ------------------------
+
+def test_laser_vector_potential_values():
+    p = tiny_params(laser_amp=0.3, laser_omega=0.5, laser_duration=10.0, laser_dir=(0.0, 0.6, 0.8))
+    m = pc.Model(p)
+    assert np.all(m.laser(0.0) == 0.0) and np.all(m.laser(10.5) == 0.0) and np.all(m.laser(-1.0) == 0.0)
+    t = 2.5   # sin^2(pi / 4) = 1/2
+    expect = 0.3 * 0.5 * np.sin(0.5 * t) * np.array([0.0, 0.6, 0.8])
+    assert np.allclose(m.laser(t), expect, rtol=0, atol=1e-15)
+    assert np.all(pc.Model(tiny_params()).laser(3.0) == 0.0)      # amplitude 0: no field
+
+
+def test_free_electrons_follow_the_field():
+    """No potential, no exchange: single planewaves stay eigenstates at all times, so
+    PT-CN keeps them fixed and the energy is 2 sum_i |G_i + kappa + A(t_n)|^2 / 2 exactly."""
+    p = tiny_params(alpha=0.0, use_hartree=False, use_lda=False, well_depth=0.0, laser_amp=0.4,
+                    laser_omega=0.9, laser_duration=6.0, laser_dir=(0.6, 0.0, 0.8), dt=0.5)
+    m = pc.Model(p)
+    npw = m.grid.npw
+    pick = [0, 5, 17]
+    C0 = np.zeros((3, npw), complex)
+    for r, k in enumerate(pick):
+        C0[r, k] = 1.0
+    st = m.init_state(C0)
+    G = m.grid.gvec_basis()[pick]
+    kick = np.asarray(p.kick)
+    for n in range(1, 9):
+        st, info = m.step(st)
+        gk = G + kick[None, :] + m.laser(n * p.dt)[None, :]
+        assert abs(info.energy - float(np.sum(gk * gk))) < 1e-12
+        assert np.max(np.abs(np.abs(st.Psi[pick, range(3)]) - 1.0)) < 1e-12
+    assert np.any(m.laser(2.0) != 0.0)
+
+
+def test_laser_second_order_against_fine_exponential_integrator():
+    """Linear H(t) (wells + kinetic with the field): the density matrix after T converges
+    at second order in dt to a fine midpoint-exponential reference."""
+    T = 1.2
+    kw = dict(alpha=0.0, use_hartree=False, use_lda=False, laser_amp=0.6, laser_omega=2.0, laser_duration=1.5)
+
+    m = pc.Model(tiny_params(**kw))
+    H0 = linear_h_matrix(m)                       # kinetic with the kick alone
+    H0 = 0.5 * (H0 + H0.conj().T)
+
+    def h_at(t):                                  # the field only changes the kinetic diagonal
+        return H0 + np.diag(m.local.kin_at(m.laser(t)) - m.local.kin)
+
+    C0 = syn.initial_coefficients(m.grid.g2_basis(), 3, seed=4)
+    st0 = m.init_state(C0)
+    P0 = st0.Psi @ st0.Psi.conj().T
+    nref = 600
+    h = T / nref
+    U = np.eye(m.grid.npw, dtype=complex)
+    for k in range(nref):
+        w, V = np.linalg.eigh(h_at((k + 0.5) * h))
+        U = (V * np.exp(-1j * h * w)[None, :]) @ V.conj().T @ U
+    P_ref = U @ P0 @ U.conj().T
+    errs = []
+    for nsteps in (3, 6, 12):
+        mm = pc.Model(tiny_params(dt=T / nsteps, **kw))
+        st = mm.init_state(C0)
+        st, infos = mm.propagate(st, nsteps)
+        assert all(i.converged for i in infos)
+        errs.append(np.linalg.norm(st.Psi @ st.Psi.conj().T - P_ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, errs
