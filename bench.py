@@ -336,7 +336,7 @@ def run_gpu(args):
     # lives on the host between steps, as in checkpointed or served runs)
     e2e = None
     if not args.no_e2e:
-        psi_np, w_np = sysg.get_state()
+        psi_np, w_np, step = sysg.get_state()
         host_psi = torch.from_numpy(psi_np).pin_memory()
         host_w = torch.from_numpy(w_np).pin_memory()
         hp, hw = host_psi.numpy(), host_w.numpy()
@@ -344,9 +344,9 @@ def run_gpu(args):
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            pkg.pt_set_state(sysg.handle, hp, hw)
+            pkg.pt_set_state(sysg.handle, hp, hw, step)
             sysg.step()
-            pkg.pt_get_state(sysg.handle, hp, hw)
+            step = pkg.pt_get_state(sysg.handle, hp, hw)
         barrier()
         te = time.perf_counter() - t0
         if ws > 1:

@@ -81,6 +81,15 @@ typedef struct pt_params {
   int pair_tile;         /* orbitals per pair-tile edge (0 = automatic) */
   int pair_tiles_per_launch; /* cap on pair tiles per launch group, which sizes the pair
                               * intermediate in the workspace (0 = automatic: up to 16 GB) */
+  /* Laser pulse (Sec. 4: 380 nm, 30 fs; its shape is given only as a figure), velocity
+   * gauge: A(t) = laser_amp sin^2(pi t / laser_duration) sin(laser_omega t) laser_dir for
+   * 0 <= t <= laser_duration, 0 after; kinetic |G + kick + A(t)|^2 / 2. Step n runs from
+   * t_n = n dt to t_{n+1}: H_n uses A(t_n), the SCF and the new observables A(t_{n+1}).
+   * laser_amp = 0 switches it off. */
+  double laser_amp;      /* A0, a.u. */
+  double laser_omega;    /* carrier frequency, a.u. (380 nm: 0.1199) */
+  double laser_duration; /* pulse length T, a.u. (30 fs: 1240.4) */
+  double laser_dir[3];   /* polarisation (used as given) */
 } pt_params;
 
 typedef struct pt_system pt_system;
@@ -92,6 +101,7 @@ typedef struct pt_step_info {
   double drho;           /* last density change dV sum |rho_new - rho_old| / (2 N_e) */
   double energy;         /* total energy of the new orbitals, Ha */
   double dipole[3];      /* -dV sum_r r rho(r), r in [0, a) */
+  double time;           /* t_{n+1} = (n + 1) dt, a.u., the time of the new orbitals */
 } pt_step_info;
 
 /* Basis size for these parameters. Planewave basis of Sec. 3.1 / Sec. 4. */
@@ -161,23 +171,25 @@ pt_status pt_set_timing(pt_system* s, int enable);
 pt_status pt_get_timing(pt_system* s, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset);
 
 /* Checkpoint and resume (no counterpart in the paper). Between steps a
- * system's state is its orbitals Psi_n and W = V_X Psi_n (the exchange of
- * Eq. 3 applied to them), both npw x n_orb complex128 (interleaved re, im),
+ * system's state is its step index n (time t_n = n dt, which fixes the laser
+ * field of H_n), its orbitals Psi_n and W = V_X Psi_n (the exchange of Eq. 3
+ * applied to them), both npw x n_orb complex128 (interleaved re, im),
  * band-major.
- * pt_get_state copies both to host buffers psi_host and w_host (caller-owned,
- * npw * n_orb complex128 each; pinned memory copies fastest) and synchronises
- * the system's stream.
+ * pt_get_state copies Psi and W to host buffers psi_host and w_host
+ * (caller-owned, npw * n_orb complex128 each; pinned memory copies fastest),
+ * stores n in *step (may be NULL) and synchronises the system's stream.
  * pt_set_state uploads a state taken by pt_get_state from a system with the
  * same parameters, then rebuilds from it, without an exchange, what the next
- * step needs: the real-space orbitals, the ACE operator (-Psi^H W = L L^H,
- * xi = W L^{-H}) and the observables. The next pt_cn_step then reproduces the
- * original run bit for bit. Host buffers are read during the call only.
- * Errors: PT_ERR_INVALID for NULL arguments; PT_ERR_NOT_PD when -Psi^H W is
- * not positive definite (W is not the exchange of Psi), after which the
- * system must be given a state again (pt_set_state or pt_set_orbitals)
- * before it steps; PT_ERR_CUDA for a failed copy or launch. */
-pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host);
-pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host);
+ * step needs: the kinetic term at t_n, the real-space orbitals, the ACE
+ * operator (-Psi^H W = L L^H, xi = W L^{-H}) and the observables. The next
+ * pt_cn_step then reproduces the original run bit for bit. Host buffers are
+ * read during the call only.
+ * Errors: PT_ERR_INVALID for NULL arguments or step < 0; PT_ERR_NOT_PD when
+ * -Psi^H W is not positive definite (W is not the exchange of Psi), after
+ * which the system must be given a state again (pt_set_state or
+ * pt_set_orbitals) before it steps; PT_ERR_CUDA for a failed copy or launch. */
+pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host, int64_t* step);
+pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host, int64_t step);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * systems); differences of two readings count the launches in between. */

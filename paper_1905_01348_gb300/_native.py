@@ -50,6 +50,10 @@ class PtParams(C.Structure):
         ("relax_q0", C.c_double),
         ("pair_tile", C.c_int),
         ("pair_tiles_per_launch", C.c_int),
+        ("laser_amp", C.c_double),
+        ("laser_omega", C.c_double),
+        ("laser_duration", C.c_double),
+        ("laser_dir", C.c_double * 3),
     ]
 
 
@@ -61,11 +65,12 @@ class PtStepInfo(C.Structure):
         ("drho", C.c_double),
         ("energy", C.c_double),
         ("dipole", C.c_double * 3),
+        ("time", C.c_double),
     ]
 
     def as_dict(self) -> dict:
         return dict(scf_iters=self.scf_iters, converged=bool(self.converged), resid_norm=self.resid_norm,
-                    drho=self.drho, energy=self.energy, dipole=np.array(self.dipole[:]))
+                    drho=self.drho, energy=self.energy, dipole=np.array(self.dipole[:]), time=self.time)
 
 
 class PtError(RuntimeError):
@@ -99,8 +104,8 @@ def load() -> C.CDLL:
         "pt_propagate": (C.c_int, [vp, C.c_int, C.POINTER(PtStepInfo)]),
         "pt_get_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
         "pt_set_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
-        "pt_get_state": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
-        "pt_set_state": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "pt_get_state": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "pt_set_state": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64]),
         "pt_observables": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "pt_orbitals_device": (C.c_int, [vp, C.POINTER(vp)]),
         "pt_set_timing": (C.c_int, [vp, C.c_int]),
@@ -159,6 +164,12 @@ def make_params(d: dict) -> PtParams:
     p.relax_q0 = float(d.get("relax_q0", 1.0))
     p.pair_tile = int(d.get("pair_tile", 0))
     p.pair_tiles_per_launch = int(d.get("pair_tiles_per_launch", 0))
+    p.laser_amp = float(d.get("laser_amp", 0.0))
+    p.laser_omega = float(d.get("laser_omega", 0.1199))
+    p.laser_duration = float(d.get("laser_duration", 1240.4))
+    ld = d.get("laser_dir", (1.0, 0.0, 0.0))
+    for k in range(3):
+        p.laser_dir[k] = float(ld[k])
     return p
 
 
@@ -234,20 +245,23 @@ def _host_c128(a: np.ndarray, shape, name: str) -> np.ndarray:
     return a
 
 
-def pt_get_state(h, psi_out: np.ndarray, w_out: np.ndarray) -> None:
-    """Copy the state (Psi, W = V_X Psi) into caller-owned (n_orb, npw) complex128 arrays."""
+def pt_get_state(h, psi_out: np.ndarray, w_out: np.ndarray) -> int:
+    """Copy the state (Psi, W = V_X Psi) into caller-owned (n_orb, npw) complex128 arrays;
+    returns the step index n of the state (time n dt)."""
     _host_c128(psi_out, w_out.shape, "psi_out")
     _host_c128(w_out, psi_out.shape, "w_out")
+    step = C.c_int64(0)
     _check(load().pt_get_state(h, psi_out.ctypes.data_as(C.POINTER(C.c_double)),
-                               w_out.ctypes.data_as(C.POINTER(C.c_double))), h)
+                               w_out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(step)), h)
+    return step.value
 
 
-def pt_set_state(h, psi: np.ndarray, w: np.ndarray) -> None:
-    """Resume from a state taken by pt_get_state (same parameters)."""
+def pt_set_state(h, psi: np.ndarray, w: np.ndarray, step: int) -> None:
+    """Resume from a state taken by pt_get_state (same parameters) at step index `step`."""
     _host_c128(psi, w.shape, "psi")
     _host_c128(w, psi.shape, "w")
     _check(load().pt_set_state(h, psi.ctypes.data_as(C.POINTER(C.c_double)),
-                               w.ctypes.data_as(C.POINTER(C.c_double))), h)
+                               w.ctypes.data_as(C.POINTER(C.c_double)), C.c_int64(int(step))), h)
 
 
 def pt_observables(h) -> tuple[float, np.ndarray]:

@@ -54,7 +54,9 @@ struct pt_system {
   bool mixed = false;
   // device data
   int* basis = nullptr;
-  double* kin = nullptr;
+  double* kin = nullptr;            // |G + kick + A(t)|^2 / 2 of the current time
+  double* gk3 = nullptr;            // G + kick per basis vector (three arrays of npw)
+  int64_t n_step = 0;               // time index of the current orbitals: t = n_step dt
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   double* khat64 = nullptr;
@@ -138,6 +140,7 @@ static pt_status check_params(const pt_params* p, std::string* why) {
   if (p->pair_tile < 0 || p->pair_tile > pt::kTileMax) { *why = "pair_tile must be in [0, 4]"; return PT_ERR_INVALID; }
   if (p->pair_tiles_per_launch < 0) { *why = "pair_tiles_per_launch must be >= 0"; return PT_ERR_INVALID; }
   if (p->scf_max < 1 && p->scf_fixed_iters < 1) { *why = "scf_max or scf_fixed_iters must be >= 1"; return PT_ERR_INVALID; }
+  if (p->laser_amp != 0.0 && !(p->laser_duration > 0.0)) { *why = "laser_duration must be positive"; return PT_ERR_INVALID; }
   return PT_OK;
 }
 
@@ -206,6 +209,7 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   pt_system* t = sys ? sys : &dummy;
   t->basis = c.take<int>(npw);
   t->kin = c.take<double>(npw);
+  t->gk3 = c.take<double>(3 * (size_t)npw);
   t->tw64 = c.take<double2>(pt::kTwiddleTotal);
   t->tw32 = c.take<float2>(pt::kTwiddleTotal);
   if (mixed) t->khat32 = c.take<float>(N); else t->khat64 = c.take<double>(N);
@@ -658,6 +662,25 @@ static pt_status state_from_psi(pt_system* sys) {
   return PT_OK;
 }
 
+// Laser vector potential A(t) (velocity gauge; pulse shape as stated in pt.h).
+static void laser_field(const pt_params* p, double t, double a[3]) {
+  a[0] = a[1] = a[2] = 0.0;
+  if (p->laser_amp == 0.0 || t < 0.0 || t > p->laser_duration) return;
+  const double s = std::sin(M_PI * t / p->laser_duration);
+  const double f = p->laser_amp * s * s * std::sin(p->laser_omega * t);
+  for (int k = 0; k < 3; ++k) a[k] = f * p->laser_dir[k];
+}
+
+// kinetic diagonal |G + kick + A(t_n)|^2 / 2 of time index n (only with the laser on;
+// otherwise the kick-only table of the start stays)
+static pt_status set_kinetic(pt_system* sys, int64_t n) {
+  if (sys->p.laser_amp == 0.0) return PT_OK;
+  double a[3];
+  laser_field(&sys->p, (double)n * sys->p.dt, a);
+  PT_CK(pt::kinetic_shifted(sys->gk3, sys->npw, a[0], a[1], a[2], sys->kin, sys->s));
+  return PT_OK;
+}
+
 // one PT-CN step (Eq. 5, Alg. 1)
 static pt_status cn_step(pt_system* sys, pt_step_info* info) {
   const int ne = sys->ne, npw = sys->npw;
@@ -666,13 +689,16 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
   const int m = sys->p.anderson_dim;
   const long stride = n;
   if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
-  // initial residual R_n = H_n Psi_n - Psi_n (Psi_n^H H_n Psi_n) and the half step
+  // initial residual R_n = H_n Psi_n - Psi_n (Psi_n^H H_n Psi_n) and the half step (H_n at t_n)
+  PT_TRY(set_kinetic(sys, sys->n_step));
   PT_TRY(density_scf(sys, sys->rho));
   PT_TRY(local_potential(sys));
   PT_TRY(apply_local_scf(sys, sys->psi, sys->hpsi));
   PT_CK(pt::axpy(kOne, sys->wg, sys->hpsi, n, sys->s));
   PT_TRY(projection(sys, sys->psi, sys->hpsi));
   PT_CK(pt::half_step(sys->psi, sys->hpsi, hdt, sys->psi_half, n, sys->s));
+  // the SCF loop and the observables of Psi_{n+1} use H at t_{n+1}
+  PT_TRY(set_kinetic(sys, sys->n_step + 1));
   PT_CK(cudaMemcpyAsync(sys->psi_f, sys->psi_half, sizeof(double2) * n, cudaMemcpyDeviceToDevice, sys->s));
   PT_TRY(real_orbitals_scf(sys, sys->psi_f));
   sys->psi_r_current = false;
@@ -744,7 +770,9 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
   PT_TRY(orthonormalize(sys, sys->psi_f, sys->psi));
   PT_TRY(state_from_psi(sys));
   if (fixed > 0) drho = hres[1] * sys->dV / (2.0 * ne);
+  sys->n_step += 1;
   if (info) {
+    info->time = (double)sys->n_step * sys->p.dt;
     info->scf_iters = it;
     info->converged = converged ? 1 : 0;
     info->resid_norm = std::sqrt(hres[0]);
@@ -914,7 +942,7 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   basis_list(p, &idx, &g2);
   const int npw = sys->npw;
   // host tables
-  std::vector<double> kin(npw);
+  std::vector<double> kin(npw), gk3(3 * (size_t)npw);
   {
     int k = 0;
     for (int t : idx) {
@@ -922,6 +950,9 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
       const double gk0 = 2.0 * M_PI * freq(i0, p->n[0]) / p->cell[0] + p->kick[0];
       const double gk1 = 2.0 * M_PI * freq(i1, p->n[1]) / p->cell[1] + p->kick[1];
       const double gk2 = 2.0 * M_PI * freq(i2, p->n[2]) / p->cell[2] + p->kick[2];
+      gk3[k] = gk0;
+      gk3[npw + k] = gk1;
+      gk3[2 * (size_t)npw + k] = gk2;
       kin[k++] = 0.5 * (gk0 * gk0 + gk1 * gk1 + gk2 * gk2);
     }
   }
@@ -946,6 +977,8 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   cudaStream_t s = sys->s;
   PT_CK(cudaMemcpyAsync(sys->basis, idx.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
   PT_CK(cudaMemcpyAsync(sys->kin, kin.data(), sizeof(double) * npw, cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(sys->gk3, gk3.data(), sizeof(double) * gk3.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaStreamSynchronize(s));
   PT_CK(cudaMemcpyAsync(sys->tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
   PT_CK(cudaMemcpyAsync(sys->tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice, s));
   if (sys->mixed) {
@@ -1154,8 +1187,9 @@ pt_status pt_set_orbitals(pt_system* sys, const double* psi_host) {
   return PT_OK;
 }
 
-pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host) {
+pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host, int64_t* step) {
   if (sys == nullptr || psi_host == nullptr || w_host == nullptr) return PT_ERR_INVALID;
+  if (step) *step = sys->n_step;
   const size_t bytes = sizeof(double2) * sys->npw * sys->ne;
   PT_CK(cudaMemcpyAsync(psi_host, sys->psi, bytes, cudaMemcpyDeviceToHost, sys->s));
   PT_CK(cudaMemcpyAsync(w_host, sys->wg, bytes, cudaMemcpyDeviceToHost, sys->s));
@@ -1163,9 +1197,11 @@ pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host) {
   return PT_OK;
 }
 
-pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host) {
-  if (sys == nullptr || psi_host == nullptr || w_host == nullptr) return PT_ERR_INVALID;
+pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host, int64_t step) {
+  if (sys == nullptr || psi_host == nullptr || w_host == nullptr || step < 0) return PT_ERR_INVALID;
   const size_t bytes = sizeof(double2) * sys->npw * sys->ne;
+  sys->n_step = step;
+  PT_TRY(set_kinetic(sys, step));
   PT_CK(cudaMemcpyAsync(sys->psi, psi_host, bytes, cudaMemcpyHostToDevice, sys->s));
   PT_CK(cudaMemcpyAsync(sys->wg, w_host, bytes, cudaMemcpyHostToDevice, sys->s));
   PT_TRY(real_orbitals(sys, sys->psi));

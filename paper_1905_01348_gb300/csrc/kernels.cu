@@ -451,6 +451,20 @@ cudaError_t anderson_update(double2* x, const double2* r, const void* dX, const 
   return cudaGetLastError();
 }
 
+// kin[k] = |gk[k] + a|^2 / 2 with gk the basis vectors G + kick (three arrays of npw)
+__global__ void k_kinetic_shifted(const double* __restrict__ gk3, int npw, double ax, double ay, double az,
+                                  double* __restrict__ kin) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npw; k += gridDim.x * blockDim.x) {
+    const double x = gk3[k] + ax, y = gk3[npw + k] + ay, z = gk3[2 * (long)npw + k] + az;
+    kin[k] = 0.5 * (x * x + y * y + z * z);
+  }
+}
+
+cudaError_t kinetic_shifted(const double* gk3, int npw, double ax, double ay, double az, double* kin, cudaStream_t s) {
+  k_kinetic_shifted<<<nblk(npw, 256), 256, 0, s>>>(gk3, npw, ax, ay, az, kin); launched();
+  return cudaGetLastError();
+}
+
 // ---- density change, energy, dipole ---------------------------------------------------
 __global__ void k_drho(const double* __restrict__ a, const double* __restrict__ b, long N, double* __restrict__ part) {
   double acc[1] = {0.0};

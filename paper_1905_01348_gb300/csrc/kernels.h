@@ -34,6 +34,7 @@ cudaError_t anderson_solve(const double2* gram, const double2* rhs, const SlotLi
 cudaError_t anderson_update(double2* x, const double2* r, const void* dX, const void* dR, long slot_stride,
                             const SlotList& sl, const double2* gamma, int mdim, int npw, long n, double beta, int f32,
                             cudaStream_t s);
+cudaError_t kinetic_shifted(const double* gk3, int npw, double ax, double ay, double az, double* kin, cudaStream_t s);
 cudaError_t rho_change(const double* a, const double* b, long N, double* part, double* out, cudaStream_t s);
 // out8: [0] sum vion rho, [1] sum vh rho, [2] sum rho^{4/3}, [3..5] sum r rho,
 //       [6] sum kin |c|^2, [7] Re tr(negM)   (grid sums without the dV factor)

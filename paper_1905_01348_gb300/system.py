@@ -35,14 +35,14 @@ class System:
         nat.pt_set_orbitals(self.handle, psi)
 
     def get_state(self):
-        """(Psi, W = V_X Psi) as two (n_orb, npw) complex128 host arrays."""
+        """(Psi, W = V_X Psi, step index) with Psi, W as (n_orb, npw) complex128 host arrays."""
         psi = np.empty((self.n_orb, self.npw), dtype=np.complex128)
         w = np.empty_like(psi)
-        nat.pt_get_state(self.handle, psi, w)
-        return psi, w
+        step = nat.pt_get_state(self.handle, psi, w)
+        return psi, w, step
 
-    def set_state(self, psi: np.ndarray, w: np.ndarray) -> None:
-        nat.pt_set_state(self.handle, psi, w)
+    def set_state(self, psi: np.ndarray, w: np.ndarray, step: int) -> None:
+        nat.pt_set_state(self.handle, psi, w, step)
 
     def observables(self):
         return nat.pt_observables(self.handle)

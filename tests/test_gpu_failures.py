@@ -92,6 +92,7 @@ def test_scf_cap_reports_not_converged_and_advances(pkg):
 @pytest.mark.parametrize("w", [
     dict(SMALL, fock_mode="ace"),
     dict(SMALL, fock_mode="exact", precision="mixed", n=(32, 32, 32), ecut=2.0),
+    dict(SMALL, fock_mode="ace", laser_amp=0.3, laser_omega=0.8, laser_duration=20.0, dt=1.0),
 ])
 def test_checkpoint_resume_is_bitwise(pkg, w):
     """pt_get_state after one step, pt_set_state into a fresh system: the next
@@ -100,17 +101,20 @@ def test_checkpoint_resume_is_bitwise(pkg, w):
     C0 = syn.initial_coefficients(model.grid.g2_basis(), w["n_orb"], seed=6)
     a = pkg.System(w, C0)
     a.step()
-    psi1, w1 = a.get_state()
+    a.step()
+    psi1, w1, n1 = a.get_state()
+    assert n1 == 2
     e1, d1 = a.observables()
     _, info_a = a.step()
     psi2 = a.orbitals()
     b = pkg.System(w, C0[::-1].copy())    # a different start state, overwritten below
-    b.set_state(psi1, w1)
+    b.set_state(psi1, w1, n1)
     eb, db = b.observables()
     assert eb == e1 and np.array_equal(db, d1)
     _, info_b = b.step()
     assert np.array_equal(b.orbitals(), psi2)
     assert info_b["energy"] == info_a["energy"] and info_b["scf_iters"] == info_a["scf_iters"]
+    assert info_b["time"] == info_a["time"] == 3 * w.get("dt", syn.COMMON["dt"])
     a.close()
     b.close()
 
@@ -122,11 +126,11 @@ def test_set_state_refuses_inconsistent_exchange(pkg):
     model = pc.Model(pc.Params.from_dict(w))
     C0 = syn.initial_coefficients(model.grid.g2_basis(), w["n_orb"], seed=7)
     s = pkg.System(w, C0)
-    psi, wx = s.get_state()
+    psi, wx, n = s.get_state()
     with pytest.raises(pkg.PtError) as e:
-        s.set_state(psi, psi.copy())
+        s.set_state(psi, psi.copy(), n)
     assert e.value.status == pkg._native.PT_ERR_NOT_PD
-    s.set_state(psi, wx)
+    s.set_state(psi, wx, n)
     status, info = s.step()
     assert status == 0 and np.isfinite(info["energy"])
     s.close()

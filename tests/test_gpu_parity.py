@@ -169,3 +169,28 @@ def test_ptcn_steps_mixed_si8(pkg):
         assert rel(s.orbitals().T, st.Psi) < 1e-4
         assert abs(info_g["energy"] - info_o.energy) < 1e-6 * abs(info_o.energy)
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_ptcn_steps_with_laser(pkg, precision, tol):
+    """Velocity-gauge laser pulse: H_n at t_n, H_{n+1} at t_{n+1}; a strong, fast field so
+    that its time dependence matters within the steps (FP64 on the non-cubic cell, mixed on
+    the 32^3 Si8 cell)."""
+    laser = dict(laser_amp=0.5, laser_omega=0.9, laser_duration=6.0, laser_dir=(0.6, 0.0, 0.8))
+    if precision == "fp64":
+        w = dict(NONCUBIC, n_orb=6, fock_mode="exact", scf_fixed_iters=4, relax_iters=3, dt=1.0, **laser)
+    else:
+        w = syn.si_workload("si8", relax_iters=3, precision="mixed", fock_mode="ace", scf_fixed_iters=4, dt=1.0,
+                            **laser)
+    model, C0 = make(w, seed=3)
+    st = model.init_state(C0)
+    s = pkg.System(w, C0)
+    for n in range(3):
+        st, info_o = model.step(st)
+        status, info_g = s.step()
+        assert info_g["time"] == (n + 1) * w["dt"]
+        assert rel(s.orbitals().T, st.Psi) < tol
+        # mixed: FP32 rounding passes through 4 unconverged fixed-point iterations of a strong
+        # field (density change still ~0.1), hence 1e-5 on the energy rather than 1e-6
+        assert abs(info_g["energy"] - info_o.energy) < (tol if precision == "fp64" else 1e-5) * abs(info_o.energy)
+    s.close()
