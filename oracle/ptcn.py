@@ -269,6 +269,33 @@ class Model:
         new = State(Psi=Psi_next, W=W, M=M, xi=xi, energy=E, dipole=d, step=st.step + 1)
         return new, StepInfo(scf_iters=it, converged=converged, resid_norm=resid, drho=drho, energy=E, dipole=d)
 
+    # -- explicit comparison integrator ----------------------------------------
+    def h_of(self, X: np.ndarray, t: float) -> np.ndarray:
+        """H[X X^H](t) X: density, local potential and exact exchange of the columns of X
+        themselves, kinetic term at time t."""
+        kin = self.local.kin_at(self.laser(t))
+        out = self.local.apply_local(self.local.local_potential(self.density(X)), X, kin)
+        if self.p.alpha != 0.0:
+            out = out + self.vx(X, X)
+        return out
+
+    def rk4_step(self, st: State) -> tuple[State, StepInfo]:
+        """One classical 4th-order Runge-Kutta step of i dPsi/dt = H[P] Psi (Eq. 1, the explicit
+        integrator the paper compares PT-CN with in Sec. 5). The Hamiltonian of each stage is
+        built from that stage's orbitals (exact exchange); no orthonormalisation."""
+        dt = self.p.dt
+        t = st.step * dt
+        P0 = st.Psi
+        k1 = -1j * self.h_of(P0, t)
+        k2 = -1j * self.h_of(P0 + 0.5 * dt * k1, t + 0.5 * dt)
+        k3 = -1j * self.h_of(P0 + 0.5 * dt * k2, t + 0.5 * dt)
+        k4 = -1j * self.h_of(P0 + dt * k3, t + dt)
+        Psi = P0 + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        W, M, xi = self.exchange_data(Psi)
+        E, d = self.observables(Psi, M, self.kin_at_step(st.step + 1))
+        new = State(Psi=Psi, W=W, M=M, xi=xi, energy=E, dipole=d, step=st.step + 1)
+        return new, StepInfo(scf_iters=0, converged=True, resid_norm=0.0, drho=0.0, energy=E, dipole=d)
+
     def propagate(self, st: State, nsteps: int):
         infos = []
         for _ in range(int(nsteps)):

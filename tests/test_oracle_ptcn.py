@@ -14,6 +14,9 @@
   2 sum |G + kappa + A(t_n)|^2 / 2 exactly; with wells and the field the
   density matrix converges at second order to a fine midpoint-exponential
   reference of the time-dependent linear H.
+* RK4 (Sec. 5's comparison integrator): fourth order against the matrix
+  exponential for a fixed linear H; on the full nonlinear H with exact
+  exchange and the laser it agrees with PT-CN up to PT-CN's O(dt^2) error.
 """
 import numpy as np
 import pytest
@@ -173,3 +176,46 @@ def test_laser_second_order_against_fine_exponential_integrator():
         errs.append(np.linalg.norm(st.Psi @ st.Psi.conj().T - P_ref))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, errs
+
+
+# ---- RK4 (the explicit integrator the paper compares with) ---------------------------
+
+def test_rk4_fourth_order_against_matrix_exponential():
+    """Fixed linear H: the error of P(T) falls ~16x per halving of dt."""
+    T = 0.8
+    errs = []
+    for nsteps in (4, 8, 16):
+        m = pc.Model(tiny_params(alpha=0.0, use_hartree=False, use_lda=False, dt=T / nsteps))
+        C0 = syn.initial_coefficients(m.grid.g2_basis(), 3, seed=4)
+        st = m.init_state(C0)
+        P0 = st.Psi @ st.Psi.conj().T
+        H = linear_h_matrix(m)
+        w, V = np.linalg.eigh(0.5 * (H + H.conj().T))
+        U = (V * np.exp(-1j * T * w)[None, :]) @ V.conj().T
+        for _ in range(nsteps):
+            st, _ = m.rk4_step(st)
+        errs.append(np.linalg.norm(st.Psi @ st.Psi.conj().T - U @ P0 @ U.conj().T))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 13.0 < r1 < 19.0 and 13.0 < r2 < 19.0, errs
+
+
+def test_rk4_and_ptcn_agree_on_the_full_hamiltonian():
+    """Nonlinear H (Hartree, LDA, exact exchange, laser): RK4 at a small step and PT-CN at
+    steps of 4 of those give the same density matrix up to PT-CN's O(dt^2) error, which
+    shrinks 4x when both steps halve."""
+    kw = dict(fock_mode="exact", laser_amp=0.2, laser_omega=1.0, laser_duration=2.0, n_orb=3)
+    T = 0.4
+    diffs = []
+    for n_pt in (2, 4):
+        m_rk = pc.Model(tiny_params(dt=T / (4 * n_pt), **kw))
+        m_pt = pc.Model(tiny_params(dt=T / n_pt, **kw))
+        C0 = syn.initial_coefficients(m_rk.grid.g2_basis(), 3, seed=6)
+        a = m_rk.init_state(C0)
+        b = m_pt.init_state(C0)
+        for _ in range(4 * n_pt):
+            a, _ = m_rk.rk4_step(a)
+        b, infos = m_pt.propagate(b, n_pt)
+        assert all(i.converged for i in infos)
+        diffs.append(np.linalg.norm(a.Psi @ a.Psi.conj().T - b.Psi @ b.Psi.conj().T))
+    assert diffs[1] < diffs[0] / 3.0, diffs
+    assert diffs[1] < 1e-3, diffs
