@@ -101,6 +101,7 @@ def load() -> C.CDLL:
         "pt_apply_h": (C.c_int, [vp, vp, vp, C.c_int, C.c_int]),
         "pt_exchange": (C.c_int, [vp, vp]),
         "pt_cn_step": (C.c_int, [vp, C.POINTER(PtStepInfo)]),
+        "pt_rk4_step": (C.c_int, [vp, C.POINTER(PtStepInfo)]),
         "pt_propagate": (C.c_int, [vp, C.c_int, C.POINTER(PtStepInfo)]),
         "pt_get_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
         "pt_set_orbitals": (C.c_int, [vp, C.POINTER(C.c_double)]),
@@ -220,6 +221,12 @@ def pt_cn_step(h) -> tuple[int, dict]:
     info = PtStepInfo()
     st = _check(load().pt_cn_step(h, C.byref(info)), h, allow=(PT_ERR_NOT_CONVERGED,))
     return st, info.as_dict()
+
+
+def pt_rk4_step(h) -> dict:
+    info = PtStepInfo()
+    _check(load().pt_rk4_step(h, C.byref(info)), h)
+    return info.as_dict()
 
 
 def pt_propagate(h, nsteps: int) -> tuple[int, list]:

@@ -671,15 +671,17 @@ static void laser_field(const pt_params* p, double t, double a[3]) {
   for (int k = 0; k < 3; ++k) a[k] = f * p->laser_dir[k];
 }
 
-// kinetic diagonal |G + kick + A(t_n)|^2 / 2 of time index n (only with the laser on;
-// otherwise the kick-only table of the start stays)
-static pt_status set_kinetic(pt_system* sys, int64_t n) {
+// kinetic diagonal |G + kick + A(t)|^2 / 2 at time t (only with the laser on; otherwise
+// the kick-only table of the start stays)
+static pt_status set_kinetic_t(pt_system* sys, double t) {
   if (sys->p.laser_amp == 0.0) return PT_OK;
   double a[3];
-  laser_field(&sys->p, (double)n * sys->p.dt, a);
+  laser_field(&sys->p, t, a);
   PT_CK(pt::kinetic_shifted(sys->gk3, sys->npw, a[0], a[1], a[2], sys->kin, sys->s));
   return PT_OK;
 }
+
+static pt_status set_kinetic(pt_system* sys, int64_t n) { return set_kinetic_t(sys, (double)n * sys->p.dt); }
 
 // one PT-CN step (Eq. 5, Alg. 1)
 static pt_status cn_step(pt_system* sys, pt_step_info* info) {
@@ -781,6 +783,65 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
     for (int k = 0; k < 3; ++k) info->dipole[k] = sys->dipole[k];
   }
   return converged ? PT_OK : PT_ERR_NOT_CONVERGED;
+}
+
+// H[X X^H](t) X for n_orb columns X: the density, local potential and exact exchange
+// of X itself, the kinetic term at time t (the stage Hamiltonian of the RK4 step).
+static pt_status h_of_self(pt_system* sys, const double2* X, double2* out, double t) {
+  PT_TRY(set_kinetic_t(sys, t));
+  PT_TRY(real_orbitals_scf(sys, X));
+  sys->psi_r_current = false;
+  PT_TRY(density_scf(sys, sys->rho));
+  PT_TRY(local_potential(sys));
+  PT_TRY(apply_local_scf(sys, X, out));
+  if (sys->p.alpha != 0.0) PT_TRY(exchange_sym(sys, out, 1));
+  return PT_OK;
+}
+
+// One classical RK4 step of i dPsi/dt = H[P] Psi (Eq. 1; the explicit integrator of the
+// paper's Sec. 5 comparison): k_s = -i H_s Psi_s with stage orbitals Psi_1 = Psi_n,
+// Psi_2,3 = Psi_n + dt/2 k_1,2, Psi_4 = Psi_n + dt k_3 at t_n, t_n + dt/2 (twice),
+// t_n + dt; Psi_{n+1} = Psi_n + dt/6 (k_1 + 2 k_2 + 2 k_3 + k_4). k_1 uses the stored
+// exchange of Psi_n; the other stages evaluate V_X of their own orbitals.
+static pt_status rk4_step(pt_system* sys, pt_step_info* info) {
+  const long n = (long)sys->npw * sys->ne;
+  const double dt = sys->p.dt;
+  const double t = (double)sys->n_step * dt;
+  const double w[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+  const double c[3] = {0.5 * dt, 0.5 * dt, dt};
+  const double ts[4] = {t, t + 0.5 * dt, t + 0.5 * dt, t + dt};
+  PT_CK(cudaMemcpyAsync(sys->psi_f, sys->psi, sizeof(double2) * n, cudaMemcpyDeviceToDevice, sys->s));
+  for (int st = 0; st < 4; ++st) {
+    if (st == 0) {
+      PT_TRY(set_kinetic_t(sys, ts[0]));
+      if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
+      PT_TRY(density_scf(sys, sys->rho));
+      PT_TRY(local_potential(sys));
+      PT_TRY(apply_local_scf(sys, sys->psi, sys->hpsi));
+      PT_CK(pt::axpy(kOne, sys->wg, sys->hpsi, n, sys->s));
+    } else {
+      PT_TRY(h_of_self(sys, sys->tmp, sys->hpsi, ts[st]));
+    }
+    // acc += w_s (-i) H_s Psi_s; next stage Psi_n + c_s (-i) H_s Psi_s
+    PT_CK(pt::axpy(make_double2(0.0, -w[st]), sys->hpsi, sys->psi_f, n, sys->s));
+    if (st < 3) {
+      PT_CK(cudaMemcpyAsync(sys->tmp, sys->psi, sizeof(double2) * n, cudaMemcpyDeviceToDevice, sys->s));
+      PT_CK(pt::axpy(make_double2(0.0, -c[st]), sys->hpsi, sys->tmp, n, sys->s));
+    }
+  }
+  PT_CK(cudaMemcpyAsync(sys->psi, sys->psi_f, sizeof(double2) * n, cudaMemcpyDeviceToDevice, sys->s));
+  sys->n_step += 1;
+  PT_TRY(set_kinetic(sys, sys->n_step));
+  sys->psi_r_current = false;
+  PT_TRY(state_from_psi(sys));
+  if (info) {
+    *info = pt_step_info{};
+    info->converged = 1;
+    info->time = (double)sys->n_step * dt;
+    info->energy = sys->energy;
+    for (int k = 0; k < 3; ++k) info->dipole[k] = sys->dipole[k];
+  }
+  return PT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1154,6 +1215,14 @@ pt_status pt_cn_step(pt_system* sys, pt_step_info* out) {
   if (sys == nullptr) return PT_ERR_INVALID;
   pt_step_info info{};
   pt_status st = cn_step(sys, &info);
+  if (out) *out = info;
+  return st;
+}
+
+pt_status pt_rk4_step(pt_system* sys, pt_step_info* out) {
+  if (sys == nullptr) return PT_ERR_INVALID;
+  pt_step_info info{};
+  pt_status st = rk4_step(sys, &info);
   if (out) *out = info;
   return st;
 }

@@ -75,6 +75,10 @@ class System:
     def step(self):
         return nat.pt_cn_step(self.handle)
 
+    def rk4_step(self):
+        """One explicit RK4 step (the comparison integrator); returns the step info dict."""
+        return nat.pt_rk4_step(self.handle)
+
     def propagate(self, nsteps: int):
         return nat.pt_propagate(self.handle, nsteps)
 

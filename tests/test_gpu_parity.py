@@ -194,3 +194,24 @@ def test_ptcn_steps_with_laser(pkg, precision, tol):
         # field (density change still ~0.1), hence 1e-5 on the energy rather than 1e-6
         assert abs(info_g["energy"] - info_o.energy) < (tol if precision == "fp64" else 1e-5) * abs(info_o.energy)
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_rk4_steps(pkg, precision, tol):
+    """The explicit RK4 comparison integrator (stage Hamiltonians with exact exchange and the
+    laser at the stage times) against the oracle's RK4, 3 steps."""
+    laser = dict(laser_amp=0.3, laser_omega=0.9, laser_duration=6.0, laser_dir=(0.6, 0.0, 0.8))
+    if precision == "fp64":
+        w = dict(NONCUBIC, n_orb=6, relax_iters=3, dt=0.05, **laser)
+    else:
+        w = syn.si_workload("si8", relax_iters=3, precision="mixed", dt=0.05, **laser)
+    model, C0 = make(w, seed=8)
+    st = model.init_state(C0)
+    s = pkg.System(w, C0)
+    for n in range(3):
+        st, info_o = model.rk4_step(st)
+        info_g = s.rk4_step()
+        assert info_g["time"] == pytest.approx((n + 1) * w["dt"], rel=0, abs=1e-15)
+        assert rel(s.orbitals().T, st.Psi) < tol
+        assert abs(info_g["energy"] - info_o.energy) < tol * abs(info_o.energy)
+    s.close()
