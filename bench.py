@@ -30,6 +30,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Fock pair-FFT solves/s (Si216 PT-CN steps, mixed precision)"
+
+
+def metric_name(workload: str, precision: str) -> str:
+    """The metric string of the JSON line (the default run is METRIC)."""
+    names = {"si8": "Si8", "si64": "Si64", "si216": "Si216"}
+    prec = "mixed precision" if precision == "mixed" else "FP64"
+    return f"Fock pair-FFT solves/s ({names[workload]} PT-CN steps, {prec})"
 UNIT = "pair-solves/s"
 STEPS_PER_FS = 20   # 50 as per step
 
@@ -233,7 +240,7 @@ def run_reference(args):
     value = statistics.mean(r["value"] for r in res)
     n_orb = {"si8": 16, "si64": 128, "si216": 432}[args.workload]
     ms_per_step = pairs_per_exchange(n_orb) / value * 1e3
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_name(args.workload, args.precision), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, args.precision, args.gpus),
@@ -363,7 +370,8 @@ def run_gpu(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": metric_name(args.workload, args.precision), "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded random orbitals, relaxed; Gaussian-well Si supercell)",

@@ -69,7 +69,8 @@ def test_reference_arm_rank0_prints_one_line():
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["impl"] == "reference" and d["metric"] == bench.metric_name("si8", "mixed") and d["unit"] == bench.UNIT
+    assert bench.metric_name("si216", "mixed") == bench.METRIC
     assert d["higher_is_better"] is True and d["value"] > 0
     assert d["config"] == bench.workload_config("si8", "mixed", 1)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
