@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(Cfg2<L>::NT, Cfg2<L>::MINB) k_fast_f2(float2* 
                                                                          const float2* __restrict__ tw_g, int reach) {
   constexpr int NT = Cfg2<L>::NT;
   constexpr int SUB = Cfg2<L>::SUB;
+  static_assert(L % SUB == 0, "the sub-batches of SUB lines must tile the L lines of a slab exactly");
   constexpr int SLAB = L * L;
   constexpr int R1 = Plan2<L>::R1, R2 = Plan2<L>::R2;
   constexpr int W = WS<L>;
