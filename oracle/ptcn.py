@@ -43,6 +43,13 @@ Readings (the paper is silent on these details):
   kinetic term is |G + kappa + A(t)|^2 / 2. Step n runs from t_n = n dt to
   t_{n+1}: H_n uses A(t_n), H_f and the observables of Psi_{n+1} use A(t_{n+1}).
   A0 = 0 (the default) leaves the kick alone.
+* Fock grid (Sec. 4: the paper evaluates the exchange on the wavefunction grid,
+  half the density grid per axis): with ``fock_grid`` set, Eq. 3 is evaluated
+  on that grid -- orbitals placed there from their basis coefficients (the
+  basis sphere must fit), pair products, kernel and W formed there, W read back
+  on the basis sphere. Pair products then alias (their frequencies reach twice
+  the sphere's), which is the discretisation the paper uses; None keeps the
+  alias-free grid n.
 * Start state: the paper propagates from a ground state (Sec. 4: the laser
   drives a converged system). The synthetic orbitals are random, and from a
   random start the fixed point of Alg. 1 does not converge at dt = 50 as. So
@@ -98,6 +105,7 @@ class Params:
     laser_omega: float = 0.1199       # carrier frequency (a.u.): 380 nm
     laser_duration: float = 1240.4    # pulse length T (a.u.): 30 fs
     laser_dir: tuple = (1.0, 0.0, 0.0)
+    fock_grid: tuple = None           # grid of the pair FFTs; None: the grid n (alias-free)
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -132,7 +140,12 @@ class Model:
         self.grid = Grid(p.n, p.cell, p.ecut)
         self.local = hm.LocalModel(self.grid, p.atoms, p.well_depth, p.well_sigma, p.kick, p.alpha,
                                    p.use_hartree, p.use_lda)
-        self.khat = ex.screened_kernel(self.grid, p.omega)
+        self.fgrid = self.grid
+        if p.fock_grid is not None and tuple(p.fock_grid) != tuple(p.n):
+            self.fgrid = Grid(p.fock_grid, p.cell, p.ecut)
+            if not np.array_equal(self.fgrid.gvec_basis(), self.grid.gvec_basis()):
+                raise ValueError("the basis sphere does not fit on the Fock grid")
+        self.khat = ex.screened_kernel(self.fgrid, p.omega)
 
     # -- external field ---------------------------------------------------------
     def laser(self, t: float) -> np.ndarray:
@@ -154,7 +167,7 @@ class Model:
     def vx(self, C: np.ndarray, X: np.ndarray) -> np.ndarray:
         if self.p.alpha == 0.0:
             return np.zeros_like(X)
-        return ex.apply_vx(self.grid, self.khat, self.p.alpha, C, X)
+        return ex.apply_vx(self.fgrid, self.khat, self.p.alpha, C, X)
 
     def exchange_data(self, C: np.ndarray):
         """W = V_X C, M = C^H W and the ACE projector (None when alpha = 0 or mode is exact)."""
@@ -162,7 +175,7 @@ class Model:
             W = np.zeros_like(C)
             return W, np.zeros((C.shape[1], C.shape[1]), complex), None
         if self.p.fock_mode == "ace":
-            W, M, _, xi = ex.build_ace(self.grid, self.khat, self.p.alpha, C)
+            W, M, _, xi = ex.build_ace(self.fgrid, self.khat, self.p.alpha, C)
             return W, M, xi
         W = self.vx(C, C)
         return W, C.conj().T @ W, None

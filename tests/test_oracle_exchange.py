@@ -10,6 +10,9 @@
 * Structure: <a|V_X b> is Hermitian and negative semidefinite (Khat > 0), and
   tr(Psi^H V_X Psi) is real.
 * ACE: K_ACE Psi = V_X Psi, xi^H Psi = -L^H, K_ACE Hermitian and NSD.
+* Fock grid (the paper's wavefunction grid): on a grid that holds the orbitals
+  but aliases their pair products, the FFT pair loop equals the same double
+  sum with every frequency folded modulo the grid.
 """
 import numpy as np
 import pytest
@@ -131,3 +134,67 @@ def test_ace_on_si_cell_uses_symmetric_pairs():
     v01 = ex.poisson_like(np.conj(psi[0]) * psi[1], khat)
     v10 = ex.poisson_like(np.conj(psi[1]) * psi[0], khat)
     assert np.max(np.abs(v10 - np.conj(v01))) < 1e-13 * np.max(np.abs(v01))
+
+
+def direct_vx_folded(grid_c, C, X, alpha, omega):
+    """The same double sum on a grid that does not hold the pair products: every frequency
+    is taken modulo the grid (its representative in the FFT range), as the grid's DFT does."""
+    n = np.asarray(grid_c.n)
+    m = np.stack(np.unravel_index(grid_c.basis, grid_c.n), axis=-1)
+    m = np.where(m < (n + 1) // 2, m, m - n)
+    keys = [tuple(v) for v in m]
+    cellv = np.asarray(grid_c.cell)
+
+    def rep(q):                                  # representative of q modulo the grid
+        q = np.mod(np.asarray(q), n)
+        return tuple(np.where(q < (n + 1) // 2, q, q - n))
+
+    def khat(q):
+        g = 2 * np.pi * np.asarray(q) / cellv
+        g2 = float(g @ g)
+        if g2 == 0.0:
+            return np.pi / omega ** 2
+        return 4 * np.pi * (1 - np.exp(-g2 / (4 * omega ** 2))) / g2
+
+    ne = C.shape[1]
+    out = np.zeros_like(X)
+    for j in range(X.shape[1]):
+        for i in range(ne):
+            rho = {}
+            for a, G in enumerate(keys):          # rho_ij(q) = Omega^-1 sum c_i^*(G) x_j(G'), G' - G = q mod n
+                for b, G1 in enumerate(keys):
+                    q = rep(np.subtract(G1, G))
+                    rho[q] = rho.get(q, 0j) + np.conj(C[a, i]) * X[b, j] / grid_c.volume
+            for q in rho:
+                rho[q] *= khat(q)
+            for a, G in enumerate(keys):          # W_j(G'') += c_i(G) v_ij(q), G + q = G'' mod n
+                for q, v in rho.items():
+                    g2 = rep(np.add(G, q))
+                    if g2 in keys:
+                        out[keys.index(g2), j] += -alpha * C[a, i] * v
+    return out
+
+
+def test_vx_on_an_aliasing_fock_grid():
+    """Eq. 3 on a grid that holds the orbitals but not their pair products (the paper's
+    choice of evaluating the exchange on the wavefunction grid): the FFT pair loop equals
+    the folded reciprocal-space double sum, and differs from the alias-free result."""
+    fine = Grid((12, 16, 10), CELL, ECUT)
+    coarse = Grid((6, 6, 4), CELL, ECUT)
+    assert fine.alias_free() and not coarse.alias_free()
+    assert np.array_equal(coarse.gvec_basis(), fine.gvec_basis())
+    C = syn.gaussian_vectors((fine.npw, 2), seed=21)
+    X = syn.gaussian_vectors((fine.npw, 2), seed=22)
+    got = ex.apply_vx(coarse, ex.screened_kernel(coarse, OMEGA), ALPHA, C, X)
+    ref = direct_vx_folded(coarse, C, X, ALPHA, OMEGA)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    exact = ex.apply_vx(fine, ex.screened_kernel(fine, OMEGA), ALPHA, C, X)
+    assert np.max(np.abs(got - exact)) > 1e-3 * np.max(np.abs(exact))
+
+
+def test_fock_grid_must_hold_the_sphere():
+    from oracle import ptcn as pc
+    base = dict(n=(12, 16, 10), cell=CELL, ecut=ECUT, atoms=np.zeros((1, 3)), n_orb=2, relax_iters=0)
+    pc.Model(pc.Params(fock_grid=(6, 6, 4), **base))
+    with pytest.raises(ValueError):
+        pc.Model(pc.Params(fock_grid=(4, 4, 4), **base))
