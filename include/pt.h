@@ -90,6 +90,11 @@ typedef struct pt_params {
   double laser_omega;    /* carrier frequency, a.u. (380 nm: 0.1199) */
   double laser_duration; /* pulse length T, a.u. (30 fs: 1240.4) */
   double laser_dir[3];   /* polarisation (used as given) */
+  /* Grid of the pair FFTs of the exchange (Eq. 3). All 0: the grid n (alias-free for the
+   * workloads). Otherwise a grid that must hold the basis sphere but may alias the pair
+   * products, as the paper's exchange on its wavefunction grid (Sec. 4); the orbitals are
+   * transformed onto it for every exchange. pt_exchange_static does not support it. */
+  int n_fock[3];
 } pt_params;
 
 typedef struct pt_system pt_system;

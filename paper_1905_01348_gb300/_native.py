@@ -54,6 +54,7 @@ class PtParams(C.Structure):
         ("laser_omega", C.c_double),
         ("laser_duration", C.c_double),
         ("laser_dir", C.c_double * 3),
+        ("n_fock", C.c_int * 3),
     ]
 
 
@@ -171,6 +172,9 @@ def make_params(d: dict) -> PtParams:
     ld = d.get("laser_dir", (1.0, 0.0, 0.0))
     for k in range(3):
         p.laser_dir[k] = float(ld[k])
+    nf = d.get("fock_grid") or (0, 0, 0)
+    for k in range(3):
+        p.n_fock[k] = int(nf[k])
     return p
 
 

@@ -79,7 +79,17 @@ struct pt_system {
   pt::SphereTables sph{};
   int *sph_row_idx = nullptr, *sph_row_kbeg = nullptr, *sph_krow = nullptr, *sph_planes = nullptr;
   unsigned char *sph_rowlive = nullptr, *sph_planelive = nullptr;
-  void *w_r = nullptr, *x_r = nullptr, *scratch = nullptr;
+  void *w_r = nullptr, *x_r = nullptr, *scratch = nullptr;   // on the Fock grid
+  // Fock grid of the pair FFTs (the main grid unless n_fock is set)
+  bool fock_own = false;
+  Grid3 gf{};
+  long Nf = 0;
+  int* basis_f = nullptr;           // flat index of each basis vector on the Fock grid
+  void* psi_rf = nullptr;           // real-space orbitals on the Fock grid (exchange precision)
+  bool use_sphere_f = false;
+  pt::SphereTables sphf{};
+  int *sphf_row_idx = nullptr, *sphf_row_kbeg = nullptr, *sphf_krow = nullptr, *sphf_planes = nullptr;
+  unsigned char *sphf_rowlive = nullptr, *sphf_planelive = nullptr;
   double2 *S = nullptr, *Mneg = nullptr, *Linv = nullptr, *Z = nullptr, *gemm_ws = nullptr;
   size_t gemm_ws_elems = 0;
   double2 *gram = nullptr, *rhs = nullptr, *gamma = nullptr;
@@ -141,6 +151,11 @@ static pt_status check_params(const pt_params* p, std::string* why) {
   if (p->pair_tiles_per_launch < 0) { *why = "pair_tiles_per_launch must be >= 0"; return PT_ERR_INVALID; }
   if (p->scf_max < 1 && p->scf_fixed_iters < 1) { *why = "scf_max or scf_fixed_iters must be >= 1"; return PT_ERR_INVALID; }
   if (p->laser_amp != 0.0 && !(p->laser_duration > 0.0)) { *why = "laser_duration must be positive"; return PT_ERR_INVALID; }
+  {
+    const bool any = p->n_fock[0] || p->n_fock[1] || p->n_fock[2];
+    for (int k = 0; k < 3 && any; ++k)
+      if (!supported_n(p->n_fock[k])) { *why = "n_fock must be all 0 or supported grid sizes"; return PT_ERR_INVALID; }
+  }
   return PT_OK;
 }
 
@@ -162,6 +177,24 @@ static void basis_list(const pt_params* p, std::vector<int>* idx, std::vector<do
           if (g2out) g2out->push_back(gg);
         }
       }
+}
+
+// The parameters with the Fock grid as the grid (for its basis listing and sizes).
+static pt_params fock_params(const pt_params* p) {
+  pt_params q = *p;
+  if (p->n_fock[0] || p->n_fock[1] || p->n_fock[2])
+    for (int k = 0; k < 3; ++k) q.n[k] = p->n_fock[k];
+  return q;
+}
+
+static bool fock_is_own(const pt_params* p) {
+  const pt_params q = fock_params(p);
+  return q.n[0] != p->n[0] || q.n[1] != p->n[1] || q.n[2] != p->n[2];
+}
+
+static long fock_points(const pt_params* p) {
+  const pt_params q = fock_params(p);
+  return (long)q.n[0] * q.n[1] * q.n[2];
 }
 
 // Twice the largest |g2| over the basis: the reach of pair products along axis 2.
@@ -203,7 +236,9 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
   const int tile = choose_tile(p);
   const long nb = (ne + tile - 1) / tile;
-  const int tpl = tiles_per_launch(p, N, mixed);
+  const long Nf = fock_points(p);
+  const bool own = fock_is_own(p);
+  const int tpl = tiles_per_launch(p, Nf, mixed);
   const int hb = h_batch(p);
   pt_system dummy;
   pt_system* t = sys ? sys : &dummy;
@@ -212,7 +247,7 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
   t->gk3 = c.take<double>(3 * (size_t)npw);
   t->tw64 = c.take<double2>(pt::kTwiddleTotal);
   t->tw32 = c.take<float2>(pt::kTwiddleTotal);
-  if (mixed) t->khat32 = c.take<float>(N); else t->khat64 = c.take<double>(N);
+  if (mixed) t->khat32 = c.take<float>(Nf); else t->khat64 = c.take<double>(Nf);
   t->hfac = c.take<double>(N);
   t->kfac = c.take<double>(N);
   t->rho_mix = c.take<double>(N);
@@ -255,9 +290,21 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
     t->gb32 = c.take<float2>(pe);
     t->gs32 = c.take<float2>(ne * ne);
   }
-  t->w_r = c.take<unsigned char>((size_t)N * ne * cs);
-  t->x_r = c.take<unsigned char>((size_t)N * ne * cs);
-  t->scratch = c.take<unsigned char>((size_t)tpl * pt::kTileMax * pt::kTileMax * N * cs);
+  t->w_r = c.take<unsigned char>((size_t)Nf * ne * cs);
+  t->x_r = c.take<unsigned char>((size_t)Nf * ne * cs);
+  t->scratch = c.take<unsigned char>((size_t)tpl * pt::kTileMax * pt::kTileMax * Nf * cs);
+  if (own) {
+    const pt_params q = fock_params(p);
+    const long L0 = q.n[0], L1 = q.n[1];
+    t->basis_f = c.take<int>(npw);
+    t->psi_rf = c.take<unsigned char>((size_t)Nf * ne * cs);
+    t->sphf_row_idx = c.take<int>(L0 * L1);
+    t->sphf_row_kbeg = c.take<int>(L0 * L1 + 1);
+    t->sphf_krow = c.take<int>(npw);
+    t->sphf_planes = c.take<int>(L0);
+    t->sphf_rowlive = c.take<unsigned char>(L0 * L1);
+    t->sphf_planelive = c.take<unsigned char>(L0);
+  }
   t->S = c.take<double2>(ne * ne);
   t->Mneg = c.take<double2>(ne * ne);
   t->Linv = c.take<double2>(ne * ne);
@@ -282,35 +329,56 @@ static size_t carve(pt_system* sys, const pt_params* p, uintptr_t base) {
 static const float2* tw_for(pt_system* sys, int L, float*) { return sys->tw32 + pt::twiddle_offset(L); }
 static const double2* tw_for(pt_system* sys, int L, double*) { return sys->tw64 + pt::twiddle_offset(L); }
 
+// A grid the orbital transforms run on: the main grid (density, local potential) or
+// the Fock grid of the pair FFTs.
+struct GridView {
+  Grid3 g;
+  long N;
+  const int* basis;
+  bool use_sphere;
+  const pt::SphereTables* sph;
+};
+static GridView main_grid(pt_system* sys) { return GridView{sys->g, sys->N, sys->basis, sys->use_sphere, &sys->sph}; }
+static GridView fock_grid(pt_system* sys) {
+  if (!sys->fock_own) return main_grid(sys);
+  return GridView{sys->gf, sys->Nf, sys->basis_f, sys->use_sphere_f, &sys->sphf};
+}
+
+// real-space form (scale Omega^{-1/2}) of ncols basis-coefficient columns c on grid v
 template <typename T>
-static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst) {
-  if (sys->use_sphere) {
-    PT_CK(pt::sphere_to_real(c, sys->npw, (pt::cplx<T>*)dst, ncols, sys->g, sys->sph, sys->basis,
-                             1.0 / std::sqrt(sys->vol), tw_for(sys, sys->g.n0, (T*)nullptr), sys->s));
+static pt_status to_real(pt_system* sys, const GridView& v, const double2* c, long ncols, void* dst) {
+  if (v.use_sphere) {
+    PT_CK(pt::sphere_to_real(c, sys->npw, (pt::cplx<T>*)dst, ncols, v.g, *v.sph, v.basis, 1.0 / std::sqrt(sys->vol),
+                             tw_for(sys, v.g.n0, (T*)nullptr), sys->s));
     return PT_OK;
   }
-  PT_CK(pt::scatter_basis<T>(c, sys->npw, dst, ncols, sys->g, sys->basis, sys->npw, 1.0 / std::sqrt(sys->vol), sys->s));
-  PT_CK(pt::fft_rows<T>(dst, dst, ncols, sys->g, 1, 1.0, nullptr, sys->tw, sys->s));
-  PT_CK(pt::fft_cols<T>(dst, ncols, sys->g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
-  PT_CK(pt::fft_cols<T>(dst, ncols, sys->g, 0, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::scatter_basis<T>(c, sys->npw, dst, ncols, v.g, v.basis, sys->npw, 1.0 / std::sqrt(sys->vol), sys->s));
+  PT_CK(pt::fft_rows<T>(dst, dst, ncols, v.g, 1, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(dst, ncols, v.g, 1, 1, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(dst, ncols, v.g, 0, 1, 0, 1.0, nullptr, sys->tw, sys->s));
   return PT_OK;
 }
 
-// forward transform of src (destroyed) and gather into out (scale sqrt(Omega)/N)
 template <typename T>
-static pt_status to_basis(pt_system* sys, void* src, long ncols, double2* out, int accumulate, const double* kin,
-                          const double2* x) {
-  if (sys->use_sphere) {
-    PT_CK(pt::sphere_from_real((const pt::cplx<T>*)src, (const T*)nullptr, (pt::cplx<T>*)src, ncols, sys->g, sys->sph,
-                               sys->basis, std::sqrt(sys->vol) / sys->N, kin, x, sys->npw, out, sys->npw, accumulate,
-                               tw_for(sys, sys->g.n0, (T*)nullptr), sys->s));
+static pt_status to_real(pt_system* sys, const double2* c, long ncols, void* dst) {
+  return to_real<T>(sys, main_grid(sys), c, ncols, dst);
+}
+
+// forward transform of src on grid v (destroyed) and gather into out (scale sqrt(Omega)/N_v)
+template <typename T>
+static pt_status to_basis(pt_system* sys, const GridView& v, void* src, long ncols, double2* out, int accumulate,
+                          const double* kin, const double2* x) {
+  if (v.use_sphere) {
+    PT_CK(pt::sphere_from_real((const pt::cplx<T>*)src, (const T*)nullptr, (pt::cplx<T>*)src, ncols, v.g, *v.sph,
+                               v.basis, std::sqrt(sys->vol) / v.N, kin, x, sys->npw, out, sys->npw, accumulate,
+                               tw_for(sys, v.g.n0, (T*)nullptr), sys->s));
     return PT_OK;
   }
-  PT_CK(pt::fft_rows<T>(src, src, ncols, sys->g, 0, 1.0, nullptr, sys->tw, sys->s));
-  PT_CK(pt::fft_cols<T>(src, ncols, sys->g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
-  PT_CK(pt::fft_cols<T>(src, ncols, sys->g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
-  PT_CK(pt::gather_basis<T>(src, out, sys->npw, ncols, sys->g, sys->basis, sys->npw, std::sqrt(sys->vol) / sys->N, kin,
-                            x, sys->npw, accumulate, sys->s));
+  PT_CK(pt::fft_rows<T>(src, src, ncols, v.g, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(src, ncols, v.g, 1, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::fft_cols<T>(src, ncols, v.g, 0, 0, 0, 1.0, nullptr, sys->tw, sys->s));
+  PT_CK(pt::gather_basis<T>(src, out, sys->npw, ncols, v.g, v.basis, sys->npw, std::sqrt(sys->vol) / v.N, kin, x,
+                            sys->npw, accumulate, sys->s));
   return PT_OK;
 }
 
@@ -390,15 +458,31 @@ static pt_status apply_local(pt_system* sys, const double2* X, double2* out, int
   return PT_OK;
 }
 
-// V_X Psi for the orbitals whose real-space form is in psi_r; out = (or +=) result
+// Real-space orbitals of the coefficients `coef` (n_orb columns) on the Fock grid in the
+// exchange precision: when the Fock grid is the main grid these are psi_r32 / psi_r, which
+// the caller keeps current for `coef`; otherwise they are transformed here.
 template <typename T>
-static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
+static pt_status fock_orbitals(pt_system* sys, const double2* coef, const void** out) {
+  if (!sys->fock_own) {
+    *out = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
+    return PT_OK;
+  }
+  PT_TRY(to_real<T>(sys, fock_grid(sys), coef, sys->ne, sys->psi_rf));
+  *out = sys->psi_rf;
+  return PT_OK;
+}
+
+// V_X Psi for the orbitals Psi = coef (Eq. 3 on the Fock grid); out = (or +=) result
+template <typename T>
+static pt_status exchange_sym_t(pt_system* sys, const double2* coef, double2* out, int accumulate) {
   const size_t cs = sizeof(pt::cplx<T>);
-  PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * sys->N * sys->ne, sys->s));
-  const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
+  const GridView fv = fock_grid(sys);
+  const void* pr = nullptr;
+  PT_TRY(fock_orbitals<T>(sys, coef, &pr));
+  PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * fv.N * sys->ne, sys->s));
   const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
   if (sys->timing) PT_CK(cudaEventRecord(sys->ev0, sys->s));
-  PT_CK(pt::fock_pairs<T>(pr, nullptr, sys->w_r, nullptr, sys->plan_sym, 1, sys->g, kt, sys->scratch, sys->tw, sys->s));
+  PT_CK(pt::fock_pairs<T>(pr, nullptr, sys->w_r, nullptr, sys->plan_sym, 1, fv.g, kt, sys->scratch, sys->tw, sys->s));
   if (sys->timing) {
     PT_CK(cudaEventRecord(sys->ev1, sys->s));
     PT_CK(cudaEventSynchronize(sys->ev1));
@@ -408,15 +492,16 @@ static pt_status exchange_sym_t(pt_system* sys, double2* out, int accumulate) {
     sys->t_pairs += (long long)sys->ne * (sys->ne + 1) / 2;
     sys->t_groups += sys->plan_sym.n_launch;
   }
-  return to_basis<T>(sys, sys->w_r, sys->ne, out, accumulate, nullptr, nullptr);
+  return to_basis<T>(sys, fv, sys->w_r, sys->ne, out, accumulate, nullptr, nullptr);
 }
 
-static pt_status exchange_sym(pt_system* sys, double2* out, int accumulate) {
+static pt_status exchange_sym(pt_system* sys, const double2* coef, double2* out, int accumulate) {
   if (sys->p.alpha == 0.0) {
     if (!accumulate) PT_CK(cudaMemsetAsync(out, 0, sizeof(double2) * sys->npw * sys->ne, sys->s));
     return PT_OK;
   }
-  return sys->mixed ? exchange_sym_t<float>(sys, out, accumulate) : exchange_sym_t<double>(sys, out, accumulate);
+  return sys->mixed ? exchange_sym_t<float>(sys, coef, out, accumulate)
+                    : exchange_sym_t<double>(sys, coef, out, accumulate);
 }
 
 static pt_status ensure_plan_x(pt_system* sys, int ncols) {
@@ -424,7 +509,7 @@ static pt_status ensure_plan_x(pt_system* sys, int ncols) {
   pt::PairTile* tiles = nullptr;
   int *lf = nullptr, *lc = nullptr, nl = 0;
   const int tile = choose_tile(&sys->p);
-  const int nt = pt::fock_build_tiles(sys->ne, ncols, tile, 0, tiles_per_launch(&sys->p, sys->N, sys->mixed), &tiles,
+  const int nt = pt::fock_build_tiles(sys->ne, ncols, tile, 0, tiles_per_launch(&sys->p, sys->Nf, sys->mixed), &tiles,
                                       &lf, &lc, &nl);
   if (nt < 0 || (size_t)nt > sys->max_tiles_x) {
     std::free(tiles); std::free(lf); std::free(lc);
@@ -437,7 +522,7 @@ static pt_status ensure_plan_x(pt_system* sys, int ncols) {
   std::free(sys->plan_x.launch_first);
   std::free(sys->plan_x.launch_count);
   sys->plan_x.tile = tile;
-  sys->plan_x.tiles_per_launch = tiles_per_launch(&sys->p, sys->N, sys->mixed);
+  sys->plan_x.tiles_per_launch = tiles_per_launch(&sys->p, sys->Nf, sys->mixed);
   sys->plan_x.n_launch = nl;
   sys->plan_x.launch_first = lf;
   sys->plan_x.launch_count = lc;
@@ -451,13 +536,15 @@ static pt_status ensure_plan_x(pt_system* sys, int ncols) {
 template <typename T>
 static pt_status exchange_x_t(pt_system* sys, const double2* X, int ncols, double2* out) {
   const size_t cs = sizeof(pt::cplx<T>);
+  const GridView fv = fock_grid(sys);
   PT_TRY(ensure_plan_x(sys, ncols));
-  PT_TRY(to_real<T>(sys, X, ncols, sys->x_r));
-  PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * sys->N * ncols, sys->s));
-  const void* pr = sys->mixed ? (const void*)sys->psi_r32 : (const void*)sys->psi_r;
+  PT_TRY(to_real<T>(sys, fv, X, ncols, sys->x_r));
+  PT_CK(cudaMemsetAsync(sys->w_r, 0, cs * fv.N * ncols, sys->s));
+  const void* pr = nullptr;
+  PT_TRY(fock_orbitals<T>(sys, sys->psi, &pr));
   const T* kt = sys->mixed ? (const T*)(const void*)sys->khat32 : (const T*)(const void*)sys->khat64;
-  PT_CK(pt::fock_pairs<T>(pr, sys->x_r, nullptr, sys->w_r, sys->plan_x, 0, sys->g, kt, sys->scratch, sys->tw, sys->s));
-  return to_basis<T>(sys, sys->w_r, ncols, out, 1, nullptr, nullptr);
+  PT_CK(pt::fock_pairs<T>(pr, sys->x_r, nullptr, sys->w_r, sys->plan_x, 0, fv.g, kt, sys->scratch, sys->tw, sys->s));
+  return to_basis<T>(sys, fv, sys->w_r, ncols, out, 1, nullptr, nullptr);
 }
 
 template <typename Tc>
@@ -593,7 +680,7 @@ static pt_status ace_from_w(pt_system* sys) {
 
 // exchange data of psi (psi_r current): wg = V_X psi, then its ACE data
 static pt_status exchange_data(pt_system* sys) {
-  PT_TRY(exchange_sym(sys, sys->wg, 0));
+  PT_TRY(exchange_sym(sys, sys->psi, sys->wg, 0));
   return ace_from_w(sys);
 }
 
@@ -718,7 +805,7 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
     PT_TRY(local_potential(sys));
     PT_TRY(apply_local_scf(sys, sys->psi_f, sys->hpsi));
     if (sys->p.alpha != 0.0) {
-      if (sys->p.fock_mode == PT_FOCK_EXACT) PT_TRY(exchange_sym(sys, sys->hpsi, 1));
+      if (sys->p.fock_mode == PT_FOCK_EXACT) PT_TRY(exchange_sym(sys, sys->psi_f, sys->hpsi, 1));
       else PT_TRY(ace_apply(sys, sys->psi_f, ne, sys->hpsi));
     }
     PT_TRY(projection(sys, sys->psi_f, sys->hpsi));
@@ -794,7 +881,7 @@ static pt_status h_of_self(pt_system* sys, const double2* X, double2* out, doubl
   PT_TRY(density_scf(sys, sys->rho));
   PT_TRY(local_potential(sys));
   PT_TRY(apply_local_scf(sys, X, out));
-  if (sys->p.alpha != 0.0) PT_TRY(exchange_sym(sys, out, 1));
+  if (sys->p.alpha != 0.0) PT_TRY(exchange_sym(sys, X, out, 1));
   return PT_OK;
 }
 
@@ -955,7 +1042,7 @@ static pt_status exchange_static_body(pt_system* t, const pt_params* p, const st
   t->tw.d32 = t->tw32;
   // real-space orbitals, then the pair pipeline (it zeroes the accumulators itself)
   PT_TRY(real_orbitals(t, d_psi));
-  PT_TRY(exchange_sym(t, d_w, 0));
+  PT_TRY(exchange_sym(t, d_psi, d_w, 0));
   PT_CK(cudaStreamSynchronize(s));
   return PT_OK;
 }
@@ -996,6 +1083,43 @@ pt_status pt_workspace_size(const pt_params* p, size_t* bytes) {
   return PT_OK;
 }
 
+// Live rows (i0, i1) of the basis sphere in flat order and the live i0 planes of a cubic
+// grid of edge L, from the basis flat indices idx (ascending); uploaded to the device.
+static pt_status upload_sphere_tables(pt_system* sys, int L, const std::vector<int>& idx, int* d_row_idx,
+                                      int* d_row_kbeg, int* d_krow, int* d_planes, unsigned char* d_rowlive,
+                                      unsigned char* d_planelive, pt::SphereTables* out) {
+  const int npw = (int)idx.size();
+  cudaStream_t s = sys->s;
+  std::vector<int> row_idx, row_kbeg, krow(npw), planes;
+  std::vector<unsigned char> rowlive((size_t)L * L, 0), planelive(L, 0);
+  int prev = -1;
+  for (int k = 0; k < npw; ++k) {
+    const int row = idx[k] / L;
+    if (row != prev) {
+      row_idx.push_back(row);
+      row_kbeg.push_back(k);
+      rowlive[row] = 1;
+      planelive[row / L] = 1;
+      prev = row;
+    }
+    krow[k] = (int)row_idx.size() - 1;
+  }
+  row_kbeg.push_back(npw);
+  for (int i0 = 0; i0 < L; ++i0)
+    if (planelive[i0]) planes.push_back(i0);
+  PT_CK(cudaMemcpyAsync(d_row_idx, row_idx.data(), sizeof(int) * row_idx.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(d_row_kbeg, row_kbeg.data(), sizeof(int) * row_kbeg.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(d_krow, krow.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
+  if (!planes.empty())
+    PT_CK(cudaMemcpyAsync(d_planes, planes.data(), sizeof(int) * planes.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(d_rowlive, rowlive.data(), rowlive.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaMemcpyAsync(d_planelive, planelive.data(), planelive.size(), cudaMemcpyHostToDevice, s));
+  PT_CK(cudaStreamSynchronize(s));
+  *out = pt::SphereTables{(int)row_idx.size(), d_row_idx, d_row_kbeg, d_krow, d_rowlive, (int)planes.size(), d_planes,
+                          d_planelive};
+  return PT_OK;
+}
+
 static pt_status init_body(pt_system* sys, const double* psi0_host) {
   const pt_params* p = &sys->p;
   std::vector<int> idx;
@@ -1021,10 +1145,11 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   pt::twiddle_host(tw.data());
   std::vector<float2> tw32(pt::kTwiddleTotal);
   for (int t = 0; t < pt::kTwiddleTotal; ++t) tw32[t] = make_float2((float)tw[t].x, (float)tw[t].y);
-  // screened kernel in the pair-intermediate layout [i2][i0][i1], scaled by -alpha / N
-  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+  // screened kernel on the Fock grid in the pair-intermediate layout [i2][i0][i1],
+  // scaled by -alpha / N_f (the inverse-FFT factor)
+  const int n0 = sys->gf.n0, n1 = sys->gf.n1, n2 = sys->gf.n2;
   const double w2 = p->omega * p->omega;
-  std::vector<double> kt((size_t)sys->N);
+  std::vector<double> kt((size_t)sys->Nf);
   for (int i2 = 0; i2 < n2; ++i2)
     for (int i0 = 0; i0 < n0; ++i0)
       for (int i1 = 0; i1 < n1; ++i1) {
@@ -1033,7 +1158,7 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
         const double gz = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
         const double gg = g0 * g0 + g1 * g1 + gz * gz;
         const double k = gg > 0.0 ? 4.0 * M_PI * (-std::expm1(-gg / (4.0 * w2))) / gg : M_PI / w2;
-        kt[((size_t)i2 * n0 + i0) * n1 + i1] = -p->alpha * k / (double)sys->N;
+        kt[((size_t)i2 * n0 + i0) * n1 + i1] = -p->alpha * k / (double)sys->Nf;
       }
   cudaStream_t s = sys->s;
   PT_CK(cudaMemcpyAsync(sys->basis, idx.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
@@ -1053,36 +1178,30 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
   if (p->n_atoms > 0)
     PT_CK(cudaMemcpyAsync(sys->d_atoms, sys->atoms.data(), sizeof(double) * 3 * p->n_atoms, cudaMemcpyHostToDevice, s));
   if (pt::sphere_fast_supported(sys->g)) {
-    // live rows (i0, i1) of the basis sphere in flat order and the live i0 planes
-    const int L = n0;
-    std::vector<int> row_idx, row_kbeg, krow(npw), planes;
-    std::vector<unsigned char> rowlive((size_t)L * L, 0), planelive(L, 0);
-    int prev = -1;
-    for (int k = 0; k < npw; ++k) {
-      const int row = idx[k] / L;
-      if (row != prev) {
-        row_idx.push_back(row);
-        row_kbeg.push_back(k);
-        rowlive[row] = 1;
-        planelive[row / L] = 1;
-        prev = row;
-      }
-      krow[k] = (int)row_idx.size() - 1;
-    }
-    row_kbeg.push_back(npw);
-    for (int i0 = 0; i0 < L; ++i0)
-      if (planelive[i0]) planes.push_back(i0);
-    PT_CK(cudaMemcpyAsync(sys->sph_row_idx, row_idx.data(), sizeof(int) * row_idx.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaMemcpyAsync(sys->sph_row_kbeg, row_kbeg.data(), sizeof(int) * row_kbeg.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaMemcpyAsync(sys->sph_krow, krow.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
-    if (!planes.empty())
-      PT_CK(cudaMemcpyAsync(sys->sph_planes, planes.data(), sizeof(int) * planes.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaMemcpyAsync(sys->sph_rowlive, rowlive.data(), rowlive.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaMemcpyAsync(sys->sph_planelive, planelive.data(), planelive.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaStreamSynchronize(s));
-    sys->sph = pt::SphereTables{(int)row_idx.size(), sys->sph_row_idx, sys->sph_row_kbeg, sys->sph_krow,
-                                sys->sph_rowlive, (int)planes.size(), sys->sph_planes, sys->sph_planelive};
+    PT_TRY(upload_sphere_tables(sys, sys->g.n0, idx, sys->sph_row_idx, sys->sph_row_kbeg, sys->sph_krow,
+                                sys->sph_planes, sys->sph_rowlive, sys->sph_planelive, &sys->sph));
     sys->use_sphere = true;
+  }
+  if (sys->fock_own) {
+    // the basis on the Fock grid: the same vectors in the same order (the sphere must fit)
+    const pt_params q = fock_params(p);
+    std::vector<int> idx_f;
+    basis_list(&q, &idx_f, nullptr);
+    bool same = (int)idx_f.size() == npw;
+    for (int k = 0; same && k < npw; ++k) {
+      const int a = idx[k], b = idx_f[k];
+      same = freq(a % p->n[2], p->n[2]) == freq(b % q.n[2], q.n[2]) &&
+             freq((a / p->n[2]) % p->n[1], p->n[1]) == freq((b / q.n[2]) % q.n[1], q.n[1]) &&
+             freq(a / (p->n[1] * p->n[2]), p->n[0]) == freq(b / (q.n[1] * q.n[2]), q.n[0]);
+    }
+    if (!same) { sys->err = "the basis sphere does not fit on the Fock grid n_fock"; return PT_ERR_INVALID; }
+    PT_CK(cudaMemcpyAsync(sys->basis_f, idx_f.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
+    if (pt::sphere_fast_supported(sys->gf)) {
+      PT_TRY(upload_sphere_tables(sys, sys->gf.n0, idx_f, sys->sphf_row_idx, sys->sphf_row_kbeg, sys->sphf_krow,
+                                  sys->sphf_planes, sys->sphf_rowlive, sys->sphf_planelive, &sys->sphf));
+      sys->use_sphere_f = true;
+    }
+    PT_CK(cudaStreamSynchronize(s));
   }
   sys->tw.d64 = sys->tw64;
   sys->tw.d32 = sys->tw32;
@@ -1091,7 +1210,7 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
     pt::PairTile* tiles = nullptr;
     int *lf = nullptr, *lc = nullptr, nl = 0;
     const int tile = choose_tile(p);
-    const int tpl = tiles_per_launch(p, sys->N, sys->mixed);
+    const int tpl = tiles_per_launch(p, sys->Nf, sys->mixed);
     const int nt = pt::fock_build_tiles(sys->ne, 0, tile, 1, tpl, &tiles, &lf, &lc, &nl);
     if (nt < 0) { sys->err = "tile schedule"; return PT_ERR_INVALID; }
     PT_CK(cudaMemcpyAsync(sys->d_tiles_sym, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, s));
@@ -1142,6 +1261,12 @@ pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_wo
   sys->s = (cudaStream_t)stream;
   sys->g = Grid3{p->n[0], p->n[1], p->n[2]};
   sys->N = sys->g.N();
+  {
+    const pt_params q = fock_params(p);
+    sys->fock_own = fock_is_own(p);
+    sys->gf = Grid3{q.n[0], q.n[1], q.n[2]};
+    sys->Nf = sys->gf.N();
+  }
   std::vector<int> idx;
   basis_list(p, &idx, nullptr);
   sys->npw = (int)idx.size();
@@ -1206,7 +1331,7 @@ pt_status pt_exchange(pt_system* sys, void* d_W) {
   if (d_W == nullptr) { sys->err = "pt_exchange: NULL output"; return PT_ERR_INVALID; }
   if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
   sys->psi_r_current = true;
-  PT_TRY(exchange_sym(sys, (double2*)d_W, 0));
+  PT_TRY(exchange_sym(sys, sys->psi, (double2*)d_W, 0));
   PT_CK(cudaStreamSynchronize(sys->s));
   return PT_OK;
 }
@@ -1318,6 +1443,7 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
   pt_status st = check_params(p, &why);
   if (st != PT_OK) { g_last_error = "pt_exchange_static: " + why; return st; }
   if (d_psi == nullptr || d_w == nullptr) { g_last_error = "pt_exchange_static: NULL orbitals or output"; return PT_ERR_INVALID; }
+  if (fock_is_own(p)) { g_last_error = "pt_exchange_static: a separate Fock grid (n_fock) is not supported"; return PT_ERR_INVALID; }
   std::vector<int> idx;
   basis_list(p, &idx, nullptr);
   const long N = (long)p->n[0] * p->n[1] * p->n[2];
@@ -1343,6 +1469,8 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
   t.s = (cudaStream_t)stream;
   t.g = Grid3{p->n[0], p->n[1], p->n[2]};
   t.N = N;
+  t.gf = t.g;
+  t.Nf = N;
   t.npw = (int)idx.size();
   t.ne = p->n_orb;
   t.hb = h_batch(p);

@@ -1,4 +1,4 @@
-// Compile-time-sized line FFTs for the pair pipeline (lengths 32, 64, 96).
+// Compile-time-sized line FFTs for the pair pipeline (lengths 32, 48, 64, 96).
 //
 // Each length L = R1 * R2 is transformed by two Stockham stages (radix R1,
 // then radix R2 with sub-transform length R1), so one line costs two
@@ -51,6 +51,7 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dftc(C* v
 
 template <int L> struct Plan2;
 template <> struct Plan2<32> { static constexpr int R1 = 8, R2 = 4; };
+template <> struct Plan2<48> { static constexpr int R1 = 4, R2 = 12; };
 template <> struct Plan2<64> { static constexpr int R1 = 8, R2 = 8; };
 template <> struct Plan2<96> { static constexpr int R1 = 8, R2 = 12; };
 

@@ -1,5 +1,5 @@
 // Transforms (FP32 or FP64) between the planewave sphere and the real-space grid for
-// cubic grids of 32, 64 or 96 points (the orbital transforms of the SCF loop,
+// cubic grids of 32, 48, 64 or 96 points (the orbital transforms of the SCF loop,
 // Sec. 3.2 and 3.4: real-space orbitals for the density and exchange, and the
 // local-potential product of Eq. 2).
 //
@@ -211,7 +211,7 @@ cudaError_t to_sphere_t(const C* vol, const typename real_of<C>::type* mul, C* w
 }  // namespace
 
 bool sphere_fast_supported(Grid3 g) {
-  return g.n0 == g.n1 && g.n1 == g.n2 && (g.n0 == 32 || g.n0 == 64 || g.n0 == 96);
+  return g.n0 == g.n1 && g.n1 == g.n2 && (g.n0 == 32 || g.n0 == 48 || g.n0 == 64 || g.n0 == 96);
 }
 
 template <typename C>
@@ -221,6 +221,7 @@ static cudaError_t to_real_any(const double2* coef, long ldc, C* vol, long nvol,
   if (nvol > 65535) return cudaErrorInvalidValue;
   switch (g.n0) {
     case 32: return to_real_t<C, 32>(coef, ldc, vol, nvol, st, basis, scale, tw_L, s);
+    case 48: return to_real_t<C, 48>(coef, ldc, vol, nvol, st, basis, scale, tw_L, s);
     case 64: return to_real_t<C, 64>(coef, ldc, vol, nvol, st, basis, scale, tw_L, s);
     case 96: return to_real_t<C, 96>(coef, ldc, vol, nvol, st, basis, scale, tw_L, s);
     default: return cudaErrorInvalidValue;
@@ -236,6 +237,7 @@ static cudaError_t from_real_any(const C* vol, const typename real_of<C>::type* 
   if (nvol > 65535) return cudaErrorInvalidValue;
   switch (g.n0) {
     case 32: return to_sphere_t<C, 32>(vol, mul, work, nvol, st, basis, scale, kin, x, ldx, out, ldo, accumulate, tw_L, s);
+    case 48: return to_sphere_t<C, 48>(vol, mul, work, nvol, st, basis, scale, kin, x, ldx, out, ldo, accumulate, tw_L, s);
     case 64: return to_sphere_t<C, 64>(vol, mul, work, nvol, st, basis, scale, kin, x, ldx, out, ldo, accumulate, tw_L, s);
     case 96: return to_sphere_t<C, 96>(vol, mul, work, nvol, st, basis, scale, kin, x, ldx, out, ldo, accumulate, tw_L, s);
     default: return cudaErrorInvalidValue;

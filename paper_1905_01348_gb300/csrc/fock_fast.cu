@@ -1,5 +1,5 @@
-// FP32 pair pipeline for cubic grids of 32, 64 or 96 points per edge (the
-// Si8 / Si64 / Si216 workloads): the same three passes as fock.cu (Eq. 3,
+// FP32 pair pipeline for cubic grids of 32, 48, 64 or 96 points per edge (the
+// Si8 / Si64 / Si216 workloads, and 48 for the Si216 wavefunction grid): the same three passes as fock.cu (Eq. 3,
 // pair loop of Alg. 2) with compile-time line lengths and two-stage radix
 // plans, padded and transposed shared-memory rows (no bank conflicts), the
 // screened-kernel multiply fused between the last forward and the first
@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
 // block of 384 threads without sub-batches).
 template <int L> struct Cfg2;
 template <> struct Cfg2<32> { static constexpr int NT = 128, SUB = 32, MINB = 4; };
+template <> struct Cfg2<48> { static constexpr int NT = 192, SUB = 48, MINB = 4; };
 template <> struct Cfg2<64> { static constexpr int NT = 256, SUB = 32, MINB = 3; };
 // 96: 192 threads balance both radices (48 lines x 12 radix-8 or 8 radix-12
 // butterflies = 3 or 2 per thread) and leave room for 152 registers without spills.
@@ -314,13 +315,14 @@ static cudaError_t launch_fast(const void* psi_r, const void* x_r, void* w_occ, 
 }
 
 bool fock_fast_supported(Grid3 g) {
-  return g.n0 == g.n1 && g.n1 == g.n2 && (g.n0 == 32 || g.n0 == 64 || g.n0 == 96);
+  return g.n0 == g.n1 && g.n1 == g.n2 && (g.n0 == 32 || g.n0 == 48 || g.n0 == 64 || g.n0 == 96);
 }
 
 cudaError_t fock_pairs_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, Grid3 g,
                             const float* khat_t, void* scratch, const float2* tw_L, cudaStream_t s) {
   switch (g.n0) {
     case 32: return launch_fast<32>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
+    case 48: return launch_fast<48>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
     case 64: return launch_fast<64>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
     case 96: return launch_fast<96>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
     default: return cudaErrorInvalidValue;
