@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fock-grid", type=int, default=0,
+                    help="edge of a cubic Fock grid for the pair FFTs (0: the workload grid, the headline)")
     ap.add_argument("--ref-sample-s", type=float, default=8.0,
                     help="host seconds of oracle work per reference-arm step")
     return ap.parse_args()
@@ -67,11 +69,12 @@ def pairs_per_exchange(n_orb: int) -> int:
     return n_orb * (n_orb + 1) // 2
 
 
-def workload_config(workload: str, precision: str, world: int) -> dict:
+def workload_config(workload: str, precision: str, world: int, fock_grid: int = 0) -> dict:
     """The `config` object of the JSON line (both arms report the same one)."""
     import synthetic as syn
     w = syn.si_workload(workload, precision=precision, fock_mode="ace")
-    return {"workload": workload, "grid": list(w["n"]), "n_orb": w["n_orb"],
+    extra = {"fock_grid": [fock_grid] * 3} if fock_grid else {}
+    return {"workload": workload, "grid": list(w["n"]), **extra, "n_orb": w["n_orb"],
             "pairs_per_step": pairs_per_exchange(w["n_orb"]), "fock_mode": "ace", "precision": precision,
             "scf_tol": w["scf_tol"], "dt_au": w["dt"],
             "l2": "inputs larger than L2 (orbitals and pair intermediates are GBs)",
@@ -243,7 +246,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": metric_name(args.workload, args.precision), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, args.precision, args.gpus),
+            "config": workload_config(args.workload, args.precision, args.gpus, args.fock_grid),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res[0]["cores"], "kind": "oracle",
                              "sample": res[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -267,6 +270,8 @@ def run_gpu(args):
     pkg.load()
 
     w = syn.si_workload(args.workload, precision=args.precision, fock_mode="ace", seed=rank)
+    if args.fock_grid:
+        w["fock_grid"] = (args.fock_grid,) * 3
     params = pkg.make_params(w)
     n_orb = w["n_orb"]
     g2 = syn.basis_g2(pkg.pt_basis_indices(params), w["n"], w["cell"])
@@ -322,14 +327,21 @@ def run_gpu(args):
     # roofline of the pair pipeline (F1 + F2 + F3 of every launch group)
     peaks = measured_peaks()
     mixed = args.precision == "mixed"
-    cubic_fast = mixed and w["n"][0] == w["n"][1] == w["n"][2] and w["n"][0] in (32, 64, 96)
-    live = live_fraction(pkg.pt_basis_indices(params), w["n"]) if cubic_fast else 1.0
-    alg_bytes_pair = pair_pipeline_bytes(w["n"], mixed, live=live)
+    nf = tuple(w.get("fock_grid") or w["n"])          # grid of the pair FFTs
+    cubic_fast = mixed and nf[0] == nf[1] == nf[2] and nf[0] in (32, 48, 64, 96)
+    live = 1.0
+    if cubic_fast:
+        # basis flat indices on the main grid -> axis-2 frequencies, then the reach on the Fock grid
+        import numpy as np
+        i2 = np.asarray(pkg.pt_basis_indices(params)) % w["n"][2]
+        f2 = np.where(i2 < (w["n"][2] + 1) // 2, i2, i2 - w["n"][2])
+        live = live_fraction(np.mod(f2, nf[2]), nf)
+    alg_bytes_pair = pair_pipeline_bytes(nf, mixed, live=live)
     pair_time_s = pair_ms / 1e3
     achieved = alg_bytes_pair * pair_count / pair_time_s / 1e9 if pair_time_s > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
-            "traffic": traffic_per_launch(args.workload, args.precision),
+            "traffic": traffic_per_launch(args.workload, args.precision) if not args.fock_grid else None,
             "kernel": "fock pair pipeline (k_fast_f1 + k_fast_f2 + k_fast_f3 at 96^3, FP32), one launch group = "
                       "one round of tiles",
             "launch_groups": groups, "pair_pipeline_ms": pair_ms, "alg_bytes_per_pair": alg_bytes_pair,
@@ -375,7 +387,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded random orbitals, relaxed; Gaussian-well Si supercell)",
-            "config": workload_config(args.workload, args.precision, ws),
+            "config": workload_config(args.workload, args.precision, ws, args.fock_grid),
             "wall_s_per_fs": ms_per_step * STEPS_PER_FS / 1e3,
             "step_latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "n": len(step_ms)},
             "scf_iters": [i["scf_iters"] for i in infos],

@@ -28,6 +28,8 @@ def main(argv=None) -> None:
     ap.add_argument("--fock-mode", default="ace", choices=["ace", "exact"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tight-tol", type=float, default=1e-9)
+    ap.add_argument("--fock-grid", type=int, default=0,
+                    help="also run mixed precision with the pair FFTs on this cubic grid and report the aliasing error")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -42,9 +44,12 @@ def main(argv=None) -> None:
     g2 = syn.basis_g2(nat.pt_basis_indices(p), base["n"], base["cell"])
     C0 = syn.initial_coefficients(g2, base["n_orb"], seed=args.seed)
     runs = {}
-    for name, prec, tol in (("fp64", "fp64", base["scf_tol"]), ("mixed", "mixed", base["scf_tol"]),
-                            ("fp64_tight", "fp64", args.tight_tol)):
-        s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200), C0)
+    cases = [("fp64", "fp64", base["scf_tol"], None), ("mixed", "mixed", base["scf_tol"], None),
+             ("fp64_tight", "fp64", args.tight_tol, None)]
+    if args.fock_grid:
+        cases.append(("mixed_fock", "mixed", base["scf_tol"], (args.fock_grid,) * 3))
+    for name, prec, tol, fock in cases:
+        s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200, fock_grid=fock), C0)
         e0, d0 = s.observables()
         rec = {"energy": [e0], "dipole": [np.asarray(d0)], "scf": [], "ms": []}
         for _ in range(args.steps):
@@ -72,6 +77,9 @@ def main(argv=None) -> None:
            "mixed_vs_fp64": compare(runs["mixed"], runs["fp64"]),
            "mixed_vs_fp64_tight": compare(runs["mixed"], ref),
            "fp64_vs_fp64_tight": compare(runs["fp64"], ref),
+           **({"mixed_fock_vs_mixed": compare(runs["mixed_fock"], runs["mixed"]),
+               "mixed_fock_vs_fp64_tight": compare(runs["mixed_fock"], ref), "fock_grid": args.fock_grid}
+              if args.fock_grid else {}),
            "energy_drift_ha_per_atom": {k: abs(r["energy"][-1] - r["energy"][0]) / n_atoms for k, r in runs.items()},
            "scf_iters": {k: r["scf"] for k, r in runs.items()},
            "ms_per_step": {k: float(np.median(r["ms"])) for k, r in runs.items()}}

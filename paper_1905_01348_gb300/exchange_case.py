@@ -26,6 +26,7 @@ def main(argv=None) -> None:
     ap.add_argument("--time", action="store_true")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--tiles-per-launch", type=int, default=0, help="cap on pair tiles per launch group (0: auto)")
+    ap.add_argument("--fock-grid", type=int, default=0, help="edge of a cubic Fock grid for the pair FFTs (0: the grid)")
     args = ap.parse_args(argv)
 
     import torch
@@ -36,6 +37,8 @@ def main(argv=None) -> None:
     nat.load()
     w = syn.si_workload(args.workload, precision=args.precision, relax_iters=0, n_orb=args.n_orb)
     w["pair_tiles_per_launch"] = args.tiles_per_launch
+    if args.fock_grid:
+        w["fock_grid"] = (args.fock_grid,) * 3
     p = make_params(w)
     g2 = syn.basis_g2(nat.pt_basis_indices(p), w["n"], w["cell"])
     C0 = syn.initial_coefficients(g2, w["n_orb"], seed=0)
