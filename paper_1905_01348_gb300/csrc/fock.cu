@@ -197,15 +197,15 @@ cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_
   const size_t smem2 = (size_t)(g.n0 + g.n1 + g.n0 * g.n1) * sizeof(C);
   if (thr13 > 1024 || thr2 > 768) return cudaErrorInvalidConfiguration;
   cudaError_t e;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[fp64]) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (const unsigned long long bit = device_bit_todo(attr_done)) {
     e = cudaFuncSetAttribute(k_fock_f1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fock_f2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fock_f3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_done[fp64] = true;
+    attr_done.fetch_or(bit, std::memory_order_release);
   }
   if (smem13 > 200 * 1024 || smem2 > 200 * 1024) return cudaErrorInvalidConfiguration;
   const C* tw0 = twp<T>(tw, g.n0);

@@ -287,15 +287,15 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f3(const float2* __res
 template <int L>
 static cudaError_t launch_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan,
                                const float* khat_t, void* scratch, const float2* tw, cudaStream_t s) {
-  static bool init = false;
-  if (!init) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (const unsigned long long bit = device_bit_todo(attr_done)) {
     cudaError_t e = cudaFuncSetAttribute(k_fast_f1<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f2<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
     if (e != cudaSuccess) return e;
-    init = true;
+    attr_done.fetch_or(bit, std::memory_order_release);
   }
   float2* X = (float2*)scratch;
   const int reach = 2 * plan.g2_reach + 1 < L ? plan.g2_reach : L;

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <string>
+#include <atomic>
 
 namespace pt {
 
@@ -157,6 +158,16 @@ cudaError_t tri_inverse(const double2* L, double2* Linv, int n, cudaStream_t s);
 cudaError_t reduce_norm2(const double2* x, long n, double* partials, int npart, double* out, cudaStream_t s);
 
 std::string cuda_msg(cudaError_t e);
+
+// One-time per-device setup (kernel attributes, occupancy queries): bit d of `mask`
+// records that device d (d < 64) is done. Returns the current device's bit, or 0
+// when the setup is already done for it.
+inline unsigned long long device_bit_todo(const std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const unsigned long long bit = 1ull << (dev & 63);
+  return (mask.load(std::memory_order_acquire) & bit) ? 0ull : bit;
+}
 
 // Count of kernels this library has launched (all systems, this process).
 void launched(int n = 1);

@@ -217,13 +217,16 @@ static cudaError_t gemm_impl(int opA, int opB, int M, int N, int K, double2 alph
   const long tiles = structure == GEMM_HERM ? (long)tm * (tm + 1) / 2 * batch : (long)tm * tn * batch;
   // split the reduction so that tiles x ksplit fills the resident block slots once
   // (a second, mostly empty wave would cost as much as the first)
-  static int slots = 0;
+  static std::atomic<int> slot_count[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  int slots = slot_count[dev & 63].load(std::memory_order_relaxed);
   if (slots == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm<Tc, TI>, 256, 0);
     slots = std::max(1, sms * std::max(1, per_sm));
+    slot_count[dev & 63].store(slots, std::memory_order_relaxed);
   }
   int ksplit = 1;
   if (K > 1024 && tiles < slots) {
