@@ -26,15 +26,17 @@ template <int L> constexpr int WS = L + 1;   // work-buffer row stride (complex 
 
 template <int L> constexpr size_t smem13() { return sizeof(float2) * (size_t)(L + NPAIR * RR * WS<L>); }
 
-// X row runs and the F1 / F3 work buffer. The work buffer holds row l = 4 p + r
-// (pair p, grid row r) at stride L + 1, so the FFT stages, which read one element
-// of 16 consecutive rows per half-warp, are bank-conflict free. The X loads and
-// stores move runs of RR = 4 values (the 4 rows) per (pair, i2); a half-warp
-// covers 4 runs. Taking those 4 runs at i2 = 16 g + 4 a + b with a = 0..3
-// (rather than 4 consecutive i2) spreads its 16 shared-memory accesses, at
-// (4 p + r)(L + 1) + i2, over 16 distinct bank pairs.
-static_assert(RR == 4, "the X run order assumes 4 rows per run");
-__device__ __forceinline__ int xrun_i2(int q) { return (q & ~15) | ((q & 3) << 2) | ((q >> 2) & 3); }
+// Row layout of the F1 / F3 work buffer: row l (pair p, grid row r) at stride
+// L + 1, and inside each aligned group of 16 elements the 4 x 4 block is
+// transposed (element 4a + b sits at 4b + a). FFT stages access one element of
+// 16 consecutive rows per half-warp (distinct banks through the odd stride);
+// the X loads and stores access 4 rows x 4 consecutive elements per half-warp,
+// which the transpose also spreads over 16 distinct bank pairs.
+template <int L> struct RowsT {
+  __device__ __forceinline__ static int at(int l, int e) {
+    return l * WS<L> + ((e & ~15) | ((e & 3) << 2) | ((e >> 2) & 3));
+  }
+};
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
                                                           const PairTile* __restrict__ tiles, int tile0,
                                                           float2* __restrict__ X, const float2* __restrict__ tw_g,
                                                           int reach) {
-  using A = Strided<WS<L>, 1>;
+  using A = RowsT<L>;
   constexpr int NT = Cfg<L>::NT13;
   constexpr int ROW = RR * L;
   constexpr long N = (long)L * L * L;
@@ -123,14 +125,13 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
   }
   __syncthreads();
   ct_forward_lay<float2, L, NPAIR * RR, NT, A>(work, np * RR, tw, tid);
-  // each (pair, i2) writes one run of RR values along i1 (see xrun_i2 for the lane order)
+  // lanes: r fastest, then i2, so each (pair, i2) writes one run of RR values along i1
   const long slot0 = (long)blockIdx.y * NPAIR;
+  const int r = tid % RR;
   for (int p = 0; p < np; ++p) {
-    float2* xp = X + (slot0 + p) * N + (long)i0 * L + i1s;
-    for (int it = tid; it < RR * L; it += NT) {
-      const int r = it % RR, i2 = xrun_i2(it / RR);
-      if (!dead_slab<L>(i2, reach)) xp[(long)i2 * L * L + r] = work[A::at(p * RR + r, i2)];
-    }
+    float2* xp = X + (slot0 + p) * N + (long)i0 * L + i1s + r;
+    for (int i2 = tid / RR; i2 < L; i2 += NT / RR)
+      if (!dead_slab<L>(i2, reach)) xp[(long)i2 * L * L] = work[A::at(p * RR + r, i2)];
   }
 }
 
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f3(const float2* __res
                                                           float2* __restrict__ w_x, const PairTile* __restrict__ tiles,
                                                           int tile0, const float2* __restrict__ X,
                                                           const float2* __restrict__ tw_g, int reach) {
-  using A = Strided<WS<L>, 1>;
+  using A = RowsT<L>;
   constexpr int NT = Cfg<L>::NT13;
   constexpr int ROW = RR * L;
   constexpr long N = (long)L * L * L;
@@ -222,13 +223,13 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f3(const float2* __res
   const long roff = ((long)i0 * L + i1s) * L;
   const int np = tl.n_pairs;
   const long slot0 = (long)blockIdx.y * NPAIR;
+  const int r = tid % RR;
   for (int p = 0; p < np; ++p) {
-    const float2* xp = X + (slot0 + p) * N + (long)i0 * L + i1s;
-    for (int it = tid; it < RR * L; it += NT) {
-      const int r = it % RR, i2 = xrun_i2(it / RR);
+    const float2* xp = X + (slot0 + p) * N + (long)i0 * L + i1s + r;
+    for (int i2 = tid / RR; i2 < L; i2 += NT / RR) {
       float2* dst = work + A::at(p * RR + r, i2);
       if (dead_slab<L>(i2, reach)) *dst = make_float2(0.f, 0.f);
-      else cp_async8(dst, xp + (long)i2 * L * L + r);
+      else cp_async8(dst, xp + (long)i2 * L * L);
     }
   }
   cp_async_wait_all();
