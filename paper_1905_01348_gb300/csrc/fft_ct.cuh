@@ -64,17 +64,9 @@ template <> struct Plan2<96> { static constexpr int R1 = 8, R2 = 12; };
 // twiddle index is uniform across the warp (a shared-memory broadcast).
 
 // Shared-memory layouts: Strided<LS, ES> puts element e of line l at
-// l * LS + e * ES. PairRows<L> holds the lines (pair p, grid row r) of a
-// pair tile as [p][e][r] with a pair stride of 4 L + 4: a half-warp of
-// consecutive lines covers 4 pairs x 4 rows at 16 distinct bank pairs, and
-// the 4 rows of one element are contiguous (16-byte vector moves).
+// l * LS + e * ES; kernels may define their own (a struct with a static at(l, e)).
 template <int LS, int ES> struct Strided {
   __device__ __forceinline__ static int at(int l, int e) { return l * LS + e * ES; }
-};
-template <int L> struct PairRows {
-  static constexpr int PS = 4 * L + 4;
-  static constexpr int SIZE = 16 * PS;
-  __device__ __forceinline__ static int at(int l, int e) { return (l >> 2) * PS + (l & 3) + e * 4; }
 };
 
 // One Stockham stage over lines [line0, line0 + nl) of length L, reading
