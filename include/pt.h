@@ -233,8 +233,10 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
 /* Release the handle (the workspace stays owned by the caller). */
 pt_status pt_destroy(pt_system* s);
 
-/* Message of the last error on this handle (or of the last failed create
- * when s is NULL). Never NULL. */
+/* Message of the last error on this handle, or, when s is NULL, of the last
+ * failed call without a handle (pt_init_system, pt_workspace_size,
+ * pt_exchange_static) on the calling thread. Never NULL; valid until the
+ * next call on the same handle or thread. */
 const char* pt_last_error(const pt_system* s);
 
 #ifdef __cplusplus

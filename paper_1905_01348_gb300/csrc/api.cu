@@ -113,7 +113,8 @@ struct pt_system {
   long long t_pairs = 0, t_groups = 0;
 };
 
-static std::string g_last_error = "no error";
+// last error of calls that have no system handle (per calling thread)
+static thread_local std::string g_last_error = "no error";
 
 #define PT_CK(call)                                                               \
   do {                                                                            \
