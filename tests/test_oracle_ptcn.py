@@ -240,3 +240,43 @@ def test_nonlinear_energy_drift_is_second_order():
         drifts.append(abs(st.energy - e0))
     r1, r2 = drifts[0] / drifts[1], drifts[1] / drifts[2]
     assert 2.8 < r1 < 5.5 and 2.8 < r2 < 5.5, drifts
+
+
+def test_anderson_fixed_point_equals_newton_solution():
+    """The PT-CN fixed point R_f(Psi_f) = 0 (Eq. 5 with exact exchange) solved by Newton's
+    method with a dense finite-difference Jacobian (real and imaginary parts as unknowns)
+    equals the oracle's Anderson iterate."""
+    p = tiny_params(dt=0.3, fock_mode="exact", omega=0.3, ecut=1.0, n_orb=2)
+    m = pc.Model(p)
+    C0 = syn.initial_coefficients(m.grid.g2_basis(), 2, seed=15)
+    st = m.init_state(C0)
+    st2, info = m.step(st)
+    assert info.converged
+
+    dt = p.dt
+    Psi_n = st.Psi
+    HP = m.apply_h(Psi_n, Psi_n, "exact")
+    Psi_half = Psi_n - 0.5j * dt * (HP - Psi_n @ (Psi_n.conj().T @ HP))
+    shape = Psi_n.shape
+
+    def resid(z):
+        Psi = (z[: z.size // 2] + 1j * z[z.size // 2:]).reshape(shape)
+        H = m.apply_h(Psi, Psi, "exact")
+        R = Psi + 0.5j * dt * (H - Psi @ (Psi.conj().T @ H)) - Psi_half
+        return np.concatenate([R.real.ravel(), R.imag.ravel()])
+
+    z = np.concatenate([Psi_half.real.ravel(), Psi_half.imag.ravel()])
+    h = 1e-6
+    for _ in range(8):
+        F = resid(z)
+        if np.linalg.norm(F) < 1e-12:
+            break
+        J = np.empty((z.size, z.size))
+        for k in range(z.size):
+            e = np.zeros(z.size)
+            e[k] = h
+            J[:, k] = (resid(z + e) - resid(z - e)) / (2 * h)
+        z = z - np.linalg.solve(J, F)
+    assert np.linalg.norm(resid(z)) < 1e-10
+    Psi_newton = pc.orthonormalize((z[: z.size // 2] + 1j * z[z.size // 2:]).reshape(shape))
+    assert np.max(np.abs(Psi_newton - st2.Psi)) < 1e-9
