@@ -235,8 +235,9 @@ pt_status pt_destroy(pt_system* s);
 
 /* Message of the last error on this handle, or, when s is NULL, of the last
  * failed call without a handle (pt_init_system, pt_workspace_size,
- * pt_exchange_static) on the calling thread. Never NULL; valid until the
- * next call on the same handle or thread. */
+ * pt_exchange_static, pt_launch_count, or any call given a NULL handle) on
+ * the calling thread. Never NULL; valid until the next call on the same
+ * handle or thread. */
 const char* pt_last_error(const pt_system* s);
 
 #ifdef __cplusplus

@@ -116,6 +116,10 @@ struct pt_system {
 // last error of calls that have no system handle (per calling thread)
 static thread_local std::string g_last_error = "no error";
 
+// Argument errors of the handle entry points: the message goes to the handle, or to the
+// calling thread's handle-less message when the handle itself is NULL.
+static pt_status invalid_arg(pt_system* sys, const char* fn, const char* what);
+
 #define PT_CK(call)                                                               \
   do {                                                                            \
     cudaError_t _e = (call);                                                      \
@@ -1289,7 +1293,7 @@ pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_wo
 }
 
 pt_status pt_build_ace(pt_system* sys) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_build_ace", "NULL handle");
   if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
   sys->psi_r_current = true;
   const int saved = sys->p.fock_mode;
@@ -1302,7 +1306,7 @@ pt_status pt_build_ace(pt_system* sys) {
 }
 
 pt_status pt_apply_h(pt_system* sys, const void* d_X, void* d_Y, int ncols, int fock_mode) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_apply_h", "NULL handle");
   if (d_X == nullptr || d_Y == nullptr || ncols < 1 || ncols > sys->ne) {
     sys->err = "pt_apply_h: need 1 <= ncols <= n_orb and non-NULL buffers";
     return PT_ERR_INVALID;
@@ -1328,7 +1332,7 @@ pt_status pt_apply_h(pt_system* sys, const void* d_X, void* d_Y, int ncols, int 
 }
 
 pt_status pt_exchange(pt_system* sys, void* d_W) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_exchange", "NULL handle");
   if (d_W == nullptr) { sys->err = "pt_exchange: NULL output"; return PT_ERR_INVALID; }
   if (!sys->psi_r_current) PT_TRY(real_orbitals(sys, sys->psi));
   sys->psi_r_current = true;
@@ -1338,7 +1342,7 @@ pt_status pt_exchange(pt_system* sys, void* d_W) {
 }
 
 pt_status pt_cn_step(pt_system* sys, pt_step_info* out) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_cn_step", "NULL handle");
   pt_step_info info{};
   pt_status st = cn_step(sys, &info);
   if (out) *out = info;
@@ -1346,7 +1350,7 @@ pt_status pt_cn_step(pt_system* sys, pt_step_info* out) {
 }
 
 pt_status pt_rk4_step(pt_system* sys, pt_step_info* out) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_rk4_step", "NULL handle");
   pt_step_info info{};
   pt_status st = rk4_step(sys, &info);
   if (out) *out = info;
@@ -1354,7 +1358,7 @@ pt_status pt_rk4_step(pt_system* sys, pt_step_info* out) {
 }
 
 pt_status pt_propagate(pt_system* sys, int nsteps, pt_step_info* out_host) {
-  if (sys == nullptr || nsteps < 0) return PT_ERR_INVALID;
+  if (sys == nullptr || nsteps < 0) return invalid_arg(sys, "pt_propagate", "NULL handle or nsteps < 0");
   pt_status worst = PT_OK;
   for (int k = 0; k < nsteps; ++k) {
     pt_step_info info{};
@@ -1367,14 +1371,14 @@ pt_status pt_propagate(pt_system* sys, int nsteps, pt_step_info* out_host) {
 }
 
 pt_status pt_get_orbitals(pt_system* sys, double* psi_host) {
-  if (sys == nullptr || psi_host == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr || psi_host == nullptr) return invalid_arg(sys, "pt_get_orbitals", "NULL handle or buffer");
   PT_CK(cudaMemcpyAsync(psi_host, sys->psi, sizeof(double2) * sys->npw * sys->ne, cudaMemcpyDeviceToHost, sys->s));
   PT_CK(cudaStreamSynchronize(sys->s));
   return PT_OK;
 }
 
 pt_status pt_set_orbitals(pt_system* sys, const double* psi_host) {
-  if (sys == nullptr || psi_host == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr || psi_host == nullptr) return invalid_arg(sys, "pt_set_orbitals", "NULL handle or buffer");
   PT_CK(cudaMemcpyAsync(sys->tmp, psi_host, sizeof(double2) * sys->npw * sys->ne, cudaMemcpyHostToDevice, sys->s));
   PT_TRY(orthonormalize(sys, sys->tmp, sys->psi));
   PT_TRY(state_from_psi(sys));
@@ -1383,7 +1387,7 @@ pt_status pt_set_orbitals(pt_system* sys, const double* psi_host) {
 }
 
 pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host, int64_t* step) {
-  if (sys == nullptr || psi_host == nullptr || w_host == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr || psi_host == nullptr || w_host == nullptr) return invalid_arg(sys, "pt_get_state", "NULL handle or buffer");
   if (step) *step = sys->n_step;
   const size_t bytes = sizeof(double2) * sys->npw * sys->ne;
   PT_CK(cudaMemcpyAsync(psi_host, sys->psi, bytes, cudaMemcpyDeviceToHost, sys->s));
@@ -1393,7 +1397,8 @@ pt_status pt_get_state(pt_system* sys, double* psi_host, double* w_host, int64_t
 }
 
 pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_host, int64_t step) {
-  if (sys == nullptr || psi_host == nullptr || w_host == nullptr || step < 0) return PT_ERR_INVALID;
+  if (sys == nullptr || psi_host == nullptr || w_host == nullptr || step < 0)
+    return invalid_arg(sys, "pt_set_state", "NULL handle or buffer, or step < 0");
   const size_t bytes = sizeof(double2) * sys->npw * sys->ne;
   sys->n_step = step;
   PT_TRY(set_kinetic(sys, step));
@@ -1408,20 +1413,20 @@ pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_h
 }
 
 pt_status pt_observables(pt_system* sys, double* energy, double* dipole) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_observables", "NULL handle");
   if (energy) *energy = sys->energy;
   if (dipole) for (int k = 0; k < 3; ++k) dipole[k] = sys->dipole[k];
   return PT_OK;
 }
 
 pt_status pt_orbitals_device(pt_system* sys, void** d_psi) {
-  if (sys == nullptr || d_psi == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr || d_psi == nullptr) return invalid_arg(sys, "pt_orbitals_device", "NULL handle or output");
   *d_psi = sys->psi;
   return PT_OK;
 }
 
 pt_status pt_set_timing(pt_system* sys, int enable) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_set_timing", "NULL handle");
   if (enable && sys->ev0 == nullptr) {
     PT_CK(cudaEventCreate(&sys->ev0));
     PT_CK(cudaEventCreate(&sys->ev1));
@@ -1431,7 +1436,7 @@ pt_status pt_set_timing(pt_system* sys, int enable) {
 }
 
 pt_status pt_get_timing(pt_system* sys, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset) {
-  if (sys == nullptr) return PT_ERR_INVALID;
+  if (sys == nullptr) return invalid_arg(sys, "pt_get_timing", "NULL handle");
   if (pair_ms) *pair_ms = sys->t_pair_ms;
   if (pairs) *pairs = sys->t_pairs;
   if (launch_groups) *launch_groups = sys->t_groups;
@@ -1491,7 +1496,7 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
 }
 
 pt_status pt_launch_count(uint64_t* count) {
-  if (count == nullptr) return PT_ERR_INVALID;
+  if (count == nullptr) return invalid_arg(nullptr, "pt_launch_count", "NULL output");
   *count = (uint64_t)pt::launch_count();
   return PT_OK;
 }
@@ -1507,6 +1512,17 @@ pt_status pt_destroy(pt_system* sys) {
   delete sys;
   return PT_OK;
 }
+
+}  // extern "C"
+
+static pt_status invalid_arg(pt_system* sys, const char* fn, const char* what) {
+  const std::string msg = std::string(fn) + ": " + what;
+  if (sys != nullptr) sys->err = msg;
+  else g_last_error = msg;
+  return PT_ERR_INVALID;
+}
+
+extern "C" {
 
 const char* pt_last_error(const pt_system* sys) {
   if (sys == nullptr) return g_last_error.c_str();

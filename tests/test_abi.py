@@ -64,3 +64,38 @@ def test_workspace_and_parameter_checks(pkg):
     with pytest.raises(pkg.PtError):
         pkg.pt_workspace_size(bad)
     assert "grid" in pkg.pt_last_error(None) or "anderson" in pkg.pt_last_error(None)
+
+
+def test_null_handle_calls_fail_with_a_message(pkg):
+    """Entry points given a NULL handle or output return PT_ERR_INVALID without touching the
+    device and leave a message naming the call in pt_last_error(NULL)."""
+    import ctypes
+    lib = ctypes.CDLL(pkg._native.LIB_PATH)
+    lib.pt_last_error.restype = ctypes.c_char_p
+    lib.pt_last_error.argtypes = [ctypes.c_void_p]
+    vp = ctypes.c_void_p
+    calls = {
+        "pt_build_ace": (),
+        "pt_apply_h": (vp(1), vp(1), 1, 0),
+        "pt_exchange": (vp(1),),
+        "pt_cn_step": (None,),
+        "pt_rk4_step": (None,),
+        "pt_propagate": (1, None),
+        "pt_get_orbitals": (vp(1),),
+        "pt_set_orbitals": (vp(1),),
+        "pt_get_state": (vp(1), vp(1), None),
+        "pt_set_state": (vp(1), vp(1), ctypes.c_int64(0)),
+        "pt_observables": (None, None),
+        "pt_orbitals_device": (vp(1),),
+        "pt_set_timing": (1,),
+        "pt_get_timing": (None, None, None, 0),
+    }
+    for name, args in calls.items():
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        assert fn(None, *args) == 1, name
+        assert lib.pt_last_error(None).decode().startswith(name + ":"), name
+    lib.pt_launch_count.restype = ctypes.c_int
+    assert lib.pt_launch_count(None) == 1
+    assert lib.pt_last_error(None).decode().startswith("pt_launch_count:")
+    assert lib.pt_destroy(None) == 0
