@@ -1,0 +1,276 @@
+"""Serving loop: PT-CN propagations admitted by device-memory footprint and run side by side.
+
+Each request asks for `steps` PT-CN steps (Eq. 5, Alg. 1) of one workload from
+seeded start orbitals. Requests are admitted in arrival order: the head of the
+queue starts as soon as it has arrived, a slot is free and its workspace
+(pt_workspace_size: orbitals, exchange and ACE data, Anderson history, pair
+intermediates) fits in what the running requests leave of the memory budget.
+An admitted request runs in its own host thread on its slot's CUDA stream, so
+its kernels overlap on the device with those of every other running request;
+its orbitals and exchange (ACE) state stay resident in its workspace from the
+first step to the last, and its memory returns to the budget when it ends.
+Requests that arrive while others run are admitted the moment a slot and
+memory free up (continuous admission, not a queue drained one at a time).
+
+The library's kernels are deterministic (no atomics; fixed reduction orders)
+and distinct systems share no device state, so a request's results are the
+same alone and in any mix; `--check-alone` re-runs every request by itself and
+reports the largest difference.
+
+    python -m paper_1905_01348_gb300.serve --requests 12 --rate 4 --steps-max 10
+
+prints one JSON object: per-step latency p50 / p99 over all steps of all
+requests, queueing delay, aggregate simulated fs per day and pair solves per
+second, the peak number of concurrent requests and the peak admitted bytes.
+"""
+from __future__ import annotations
+
+import argparse
+import collections
+import dataclasses
+import json
+import math
+import threading
+import time
+
+FS_AU = 41.341374575751   # atomic units of time per femtosecond
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    workload: str                  # "si8", "si64" or "si216"
+    steps: int
+    arrival_s: float = 0.0         # seconds after the start of the run
+    seed: int = 0                  # seed of the start orbitals
+    kick: tuple = (0.01, 0.0, 0.0)
+    precision: str = "mixed"
+
+
+@dataclasses.dataclass
+class Outcome:
+    rid: int
+    workload: str
+    footprint: int
+    arrival_s: float
+    admitted_s: float | None = None
+    finished_s: float | None = None
+    slot: int | None = None
+    step_ms: list = dataclasses.field(default_factory=list)
+    energy: list = dataclasses.field(default_factory=list)
+    dipole: list = dataclasses.field(default_factory=list)
+    scf_iters: list = dataclasses.field(default_factory=list)
+    orbitals: object = None
+    error: str | None = None
+
+
+def percentile(values, q: float) -> float | None:
+    """Nearest-rank percentile (q in (0, 1]) of a non-empty sequence; None when empty."""
+    v = sorted(values)
+    if not v:
+        return None
+    return v[min(len(v) - 1, max(0, math.ceil(q * len(v)) - 1))]
+
+
+class Server:
+    """Admits requests by footprint and runs each on its own slot (stream + host thread).
+
+    footprint(req) -> bytes a request holds while it runs; open_system(req, slot) -> an
+    object with step() -> (status, info dict with energy, dipole, scf_iters), orbitals()
+    and close(). The CUDA backend is `cuda_backend`; tests may pass host-only stand-ins.
+    """
+
+    def __init__(self, footprint, open_system, budget_bytes: int, max_active: int = 8,
+                 keep_orbitals: bool = False, clock=time.perf_counter):
+        if max_active < 1:
+            raise ValueError("max_active must be >= 1")
+        self.footprint = footprint
+        self.open_system = open_system
+        self.budget = int(budget_bytes)
+        self.max_active = int(max_active)
+        self.keep_orbitals = keep_orbitals
+        self.clock = clock
+        self.peak_active = 0
+        self.peak_bytes = 0
+        self.wall_s = 0.0
+
+    def _work(self, req: Request, out: Outcome) -> None:
+        system = None
+        try:
+            system = self.open_system(req, out.slot)
+            for _ in range(req.steps):
+                t = self.clock()
+                _, info = system.step()
+                out.step_ms.append((self.clock() - t) * 1e3)
+                out.energy.append(info["energy"])
+                out.dipole.append(list(info["dipole"]))
+                out.scf_iters.append(info["scf_iters"])
+            if self.keep_orbitals:
+                out.orbitals = system.orbitals()
+        except Exception as e:   # reported per request; the other requests carry on
+            out.error = f"{type(e).__name__}: {e}"
+        finally:
+            if system is not None:
+                try:
+                    system.close()
+                except Exception as e:
+                    out.error = out.error or f"close: {type(e).__name__}: {e}"
+
+    def run(self, requests) -> list:
+        """Serve `requests` (arrival times relative to the call); returns their outcomes
+        in the order given."""
+        reqs = list(requests)
+        out = {r.rid: Outcome(r.rid, r.workload, int(self.footprint(r)), r.arrival_s) for r in reqs}
+        pending = collections.deque(sorted(reqs, key=lambda r: (r.arrival_s, r.rid)))
+        cv = threading.Condition()
+        free_slots = list(range(self.max_active - 1, -1, -1))
+        used = [0]
+        active = [0]
+        threads = []
+        t0 = self.clock()
+
+        def finish(req, o):
+            self._work(req, o)
+            with cv:
+                o.finished_s = self.clock() - t0
+                used[0] -= o.footprint
+                active[0] -= 1
+                free_slots.append(o.slot)
+                cv.notify_all()
+
+        with cv:
+            while pending or active[0]:
+                now = self.clock() - t0
+                while pending and pending[0].arrival_s <= now and free_slots:
+                    r = pending[0]
+                    o = out[r.rid]
+                    if o.footprint > self.budget:
+                        o.error = f"footprint {o.footprint} B exceeds the budget {self.budget} B"
+                        pending.popleft()
+                        continue
+                    if used[0] + o.footprint > self.budget:
+                        break
+                    pending.popleft()
+                    o.slot = free_slots.pop()
+                    o.admitted_s = now
+                    used[0] += o.footprint
+                    active[0] += 1
+                    self.peak_active = max(self.peak_active, active[0])
+                    self.peak_bytes = max(self.peak_bytes, used[0])
+                    th = threading.Thread(target=finish, args=(r, o), daemon=True)
+                    threads.append(th)
+                    th.start()
+                if not pending and not active[0]:
+                    break
+                timeout = None
+                if pending and pending[0].arrival_s > now:
+                    timeout = pending[0].arrival_s - now
+                cv.wait(timeout=timeout)
+        for th in threads:
+            th.join()
+        self.wall_s = self.clock() - t0
+        return [out[r.rid] for r in reqs]
+
+
+def summarize(outcomes, wall_s: float, dt_au: float, pairs_of) -> dict:
+    """Latency and throughput of a served run. pairs_of(workload) = pair solves per step."""
+    steps = [ms for o in outcomes for ms in o.step_ms]
+    waits = [o.admitted_s - o.arrival_s for o in outcomes if o.admitted_s is not None]
+    n_steps = len(steps)
+    fs = n_steps * dt_au / FS_AU
+    pairs = sum(len(o.step_ms) * pairs_of(o.workload) for o in outcomes)
+    return {
+        "requests": len(outcomes), "completed": sum(1 for o in outcomes if o.error is None and o.finished_s is not None),
+        "errors": {o.rid: o.error for o in outcomes if o.error},
+        "steps": n_steps, "wall_s": wall_s,
+        "step_latency_ms": {"p50": percentile(steps, 0.50), "p99": percentile(steps, 0.99)},
+        "queue_wait_s": {"p50": percentile(waits, 0.50), "p99": percentile(waits, 0.99)},
+        "fs_per_day": fs / wall_s * 86400.0 if wall_s > 0 else None,
+        "pair_solves_per_s": pairs / wall_s if wall_s > 0 else None,
+    }
+
+
+def cuda_backend(device: str = "cuda:0", max_active: int = 8):
+    """(footprint, open_system) for the CUDA library: one torch stream per slot, the
+    workspace allocated on that stream, start orbitals from the seeded generator."""
+    import torch
+    import synthetic as syn
+    from . import _native as nat
+    from .system import System
+
+    nat.load()
+    dev = torch.device(device)
+    streams = [torch.cuda.Stream(dev) for _ in range(max_active)]
+
+    def workload(req):
+        return syn.si_workload(req.workload, precision=req.precision, fock_mode="ace", kick=tuple(req.kick))
+
+    def footprint(req):
+        return nat.pt_workspace_size(nat.make_params(workload(req)))
+
+    def open_system(req, slot):
+        torch.cuda.set_device(dev)
+        w = workload(req)
+        p = nat.make_params(w)
+        g2 = syn.basis_g2(nat.pt_basis_indices(p), w["n"], w["cell"])
+        c0 = syn.initial_coefficients(g2, w["n_orb"], seed=req.seed)
+        with torch.cuda.stream(streams[slot]):
+            return System(w, c0, device=str(dev), stream=streams[slot])
+
+    return footprint, open_system
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--requests", type=int, default=12)
+    ap.add_argument("--rate", type=float, default=4.0, help="mean arrivals per second (Poisson)")
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--workloads", default="si8,si64,si216")
+    ap.add_argument("--steps-min", type=int, default=5)
+    ap.add_argument("--steps-max", type=int, default=50)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="0: 90%% of the device's free memory")
+    ap.add_argument("--batched", action="store_true",
+                    help="12 Si8 + 12 Si64 trajectories, all at t = 0, 20 steps, kicks from seed 1")
+    ap.add_argument("--check-alone", action="store_true",
+                    help="re-run every request alone and report the largest difference of its results")
+    args = ap.parse_args(argv)
+
+    import numpy as np
+    import torch
+    import synthetic as syn
+
+    if args.batched:
+        kicks = syn.batched_kicks(24, seed=1)
+        reqs = [Request(k, "si8" if k < 12 else "si64", 20, 0.0, seed=k, kick=tuple(kicks[k]),
+                        precision=args.precision) for k in range(24)]
+    else:
+        stream = syn.request_stream(args.requests, args.rate, seed=args.seed,
+                                    workloads=tuple(args.workloads.split(",")), steps=(args.steps_min, args.steps_max))
+        reqs = [Request(d["rid"], d["workload"], d["steps"], d["arrival_s"], seed=d["seed"], precision=args.precision)
+                for d in stream]
+    budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else int(0.9 * torch.cuda.mem_get_info()[0])
+    footprint, open_system = cuda_backend(max_active=args.max_active)
+    srv = Server(footprint, open_system, budget, args.max_active, keep_orbitals=args.check_alone)
+    outs = srv.run(reqs)
+    n_orb = {k: syn.si_workload(k)["n_orb"] for k in ("si8", "si64", "si216")}
+    res = summarize(outs, srv.wall_s, syn.DT_50AS, lambda wl: n_orb[wl] * (n_orb[wl] + 1) // 2)
+    res.update({"mode": "batched" if args.batched else "poisson", "rate_per_s": None if args.batched else args.rate,
+                "precision": args.precision, "max_active": args.max_active, "budget_bytes": budget,
+                "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes})
+    if args.check_alone:
+        alone = Server(footprint, open_system, budget, 1, keep_orbitals=True)
+        worst_psi, worst_e = 0.0, 0.0
+        for r, o in zip(reqs, outs):
+            (a,) = alone.run([dataclasses.replace(r, arrival_s=0.0)])
+            if o.error or a.error:
+                continue
+            worst_psi = max(worst_psi, float(np.max(np.abs(a.orbitals - o.orbitals))))
+            worst_e = max(worst_e, float(np.max(np.abs(np.subtract(a.energy, o.energy)))))
+        res["alone_vs_mix"] = {"max_orbital_diff": worst_psi, "max_energy_diff_ha": worst_e}
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -123,3 +123,18 @@ def basis_g2(flat_index: np.ndarray, n, cell) -> np.ndarray:
         g = 2.0 * np.pi * m / float(cell[k])
         out += g * g
     return out
+
+
+def request_stream(count: int, rate_per_s: float, seed: int = 2, workloads=("si8", "si64", "si216"),
+                   steps=(5, 50)) -> list:
+    """A Poisson stream of propagation requests: exponential inter-arrival times of mean
+    1 / rate_per_s seconds, workload uniform over ``workloads``, step count uniform over
+    the integers steps[0]..steps[1], orbital seed = request index. Returns dictionaries
+    with keys rid, arrival_s, workload, steps, seed."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    gaps = rng.exponential(1.0 / float(rate_per_s), size=count)
+    arrival = np.cumsum(gaps) - gaps[0]          # the first request arrives at t = 0
+    kinds = rng.integers(0, len(workloads), size=count)
+    nsteps = rng.integers(int(steps[0]), int(steps[1]) + 1, size=count)
+    return [dict(rid=k, arrival_s=float(arrival[k]), workload=workloads[int(kinds[k])], steps=int(nsteps[k]), seed=k)
+            for k in range(count)]

@@ -1,0 +1,161 @@
+"""The serving loop's host logic on the CPU, with stand-in systems.
+
+Checked: admission in arrival order by footprint and free slots (never over the
+budget, never more than max_active at once), requests that arrive while others
+run are admitted as soon as memory frees up, oversized and failing requests are
+reported without stopping the others, and every request gets its own results
+back whatever the mix (a stand-in that steps an oracle model per request).
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from paper_1905_01348_gb300.serve import Request, Server, percentile, summarize
+
+
+class SleepSystem:
+    """step() sleeps; tracks how many systems are open at once."""
+    lock = threading.Lock()
+    open_now = 0
+    open_peak = 0
+
+    def __init__(self, req, slot, step_s=0.01, fail_at=None):
+        self.req, self.k, self.step_s, self.fail_at = req, 0, step_s, fail_at
+        with SleepSystem.lock:
+            SleepSystem.open_now += 1
+            SleepSystem.open_peak = max(SleepSystem.open_peak, SleepSystem.open_now)
+
+    def step(self):
+        time.sleep(self.step_s)
+        self.k += 1
+        if self.fail_at is not None and self.k == self.fail_at:
+            raise RuntimeError("planted failure")
+        return 0, {"energy": float(self.req.rid * 100 + self.k), "dipole": [0.0, 0.0, float(self.k)], "scf_iters": 3}
+
+    def orbitals(self):
+        return np.full(4, self.req.rid, dtype=complex)
+
+    def close(self):
+        with SleepSystem.lock:
+            SleepSystem.open_now -= 1
+
+
+def reset_counts():
+    SleepSystem.open_now = 0
+    SleepSystem.open_peak = 0
+
+
+def test_admission_by_footprint_and_slots():
+    reset_counts()
+    sizes = {0: 40, 1: 40, 2: 40, 3: 30, 4: 10}
+    steps = {0: 4, 1: 10, 2: 4, 3: 4, 4: 4}
+    reqs = [Request(k, "si8", steps[k], 0.0) for k in range(5)]
+    srv = Server(lambda r: sizes[r.rid], lambda r, s: SleepSystem(r, s), budget_bytes=100, max_active=3)
+    outs = srv.run(reqs)
+    assert all(o.error is None and len(o.step_ms) == steps[o.rid] for o in outs)
+    assert srv.peak_bytes <= 100 and srv.peak_active <= 3 and SleepSystem.open_peak <= 3
+    by = {o.rid: o for o in outs}
+    # 0 and 1 start at once; 2 must wait for memory, and 3, 4 queue behind it (arrival order)
+    assert by[0].admitted_s < 0.005 and by[1].admitted_s < 0.005
+    assert by[2].admitted_s >= min(by[0].finished_s, by[1].finished_s) - 1e-6
+    assert by[3].admitted_s >= by[2].admitted_s and by[4].admitted_s >= by[3].admitted_s
+    # 2 was admitted when 0 finished, while 1 was still running: continuous admission
+    assert by[2].admitted_s >= by[0].finished_s and by[2].admitted_s < by[1].finished_s
+    assert [o.slot for o in outs[:2]] == [0, 1]
+
+
+def test_arrivals_are_respected_and_overlap():
+    reset_counts()
+    reqs = [Request(0, "si8", 12, 0.0), Request(1, "si8", 2, 0.03), Request(2, "si8", 2, 0.06)]
+    srv = Server(lambda r: 1, lambda r, s: SleepSystem(r, s), budget_bytes=10, max_active=4)
+    outs = srv.run(reqs)
+    for r, o in zip(reqs, outs):
+        assert o.admitted_s >= r.arrival_s - 1e-9
+    # request 1 arrives while request 0 is running and starts immediately
+    assert outs[1].admitted_s < outs[0].finished_s
+    assert outs[1].admitted_s - reqs[1].arrival_s < 0.05
+    assert SleepSystem.open_peak >= 2
+
+
+def test_oversized_and_failing_requests_are_reported():
+    reset_counts()
+    sizes = {0: 500, 1: 10, 2: 10}
+    reqs = [Request(k, "si8", 3, 0.0) for k in range(3)]
+
+    def open_system(r, s):
+        return SleepSystem(r, s, fail_at=2 if r.rid == 2 else None)
+
+    srv = Server(lambda r: sizes[r.rid], open_system, budget_bytes=100, max_active=2)
+    outs = srv.run(reqs)
+    assert "exceeds the budget" in outs[0].error and outs[0].admitted_s is None
+    assert outs[1].error is None and len(outs[1].step_ms) == 3
+    assert "planted failure" in outs[2].error and len(outs[2].step_ms) == 1
+    assert SleepSystem.open_now == 0          # every opened system was closed
+    s = summarize(outs, srv.wall_s, syn.DT_50AS, lambda wl: 136)
+    assert s["completed"] == 1 and set(s["errors"]) == {0, 2} and s["steps"] == 4
+
+
+def test_percentile_and_summary():
+    assert percentile([], 0.5) is None
+    assert percentile([3.0, 1.0, 2.0], 0.5) == 2.0
+    assert percentile(list(range(1, 101)), 0.99) == 99
+    assert percentile(list(range(1, 101)), 1.0) == 100
+    reset_counts()
+    reqs = [Request(k, "si8", 5, 0.0) for k in range(2)]
+    srv = Server(lambda r: 1, lambda r, s: SleepSystem(r, s, step_s=0.002), 10, 2)
+    outs = srv.run(reqs)
+    s = summarize(outs, srv.wall_s, syn.DT_50AS, lambda wl: 136)
+    assert s["steps"] == 10 and s["completed"] == 2
+    assert s["pair_solves_per_s"] == pytest.approx(10 * 136 / srv.wall_s)
+    assert s["fs_per_day"] == pytest.approx(10 * syn.DT_50AS / 41.341374575751 / srv.wall_s * 86400)
+
+
+def test_request_stream():
+    a = syn.request_stream(4000, 4.0, seed=2)
+    assert a == syn.request_stream(4000, 4.0, seed=2)
+    t = np.array([d["arrival_s"] for d in a])
+    assert t[0] == 0.0 and np.all(np.diff(t) >= 0)
+    assert np.mean(np.diff(t)) == pytest.approx(0.25, rel=0.05)
+    kinds = [d["workload"] for d in a]
+    for k in ("si8", "si64", "si216"):
+        assert kinds.count(k) / len(kinds) == pytest.approx(1 / 3, abs=0.03)
+    steps = np.array([d["steps"] for d in a])
+    assert steps.min() == 5 and steps.max() == 50
+
+
+class OracleSystem:
+    """A stand-in that steps an oracle model (FP64 NumPy) for one request."""
+
+    def __init__(self, req, slot):
+        import oracle.ptcn as pc
+        cell, frac = syn.diamond_supercell(1)
+        p = pc.Params(n=(12, 12, 12), cell=tuple(cell), ecut=1.5, atoms=frac, n_orb=3, relax_iters=0,
+                      scf_tol=1e-10, scf_max=100, kick=tuple(req.kick), fock_mode="exact")
+        self.m = pc.Model(p)
+        self.st = self.m.init_state(syn.initial_coefficients(self.m.grid.g2_basis(), 3, seed=req.seed))
+
+    def step(self):
+        self.st, info = self.m.step(self.st)
+        return 0, {"energy": self.st.energy, "dipole": list(self.st.dipole), "scf_iters": info.scf_iters}
+
+    def orbitals(self):
+        return self.st.Psi.copy()
+
+    def close(self):
+        pass
+
+
+def test_results_are_the_same_alone_and_in_the_mix():
+    kicks = syn.batched_kicks(4, seed=1)
+    reqs = [Request(k, "si8", 2 + k % 2, 0.01 * k, seed=k, kick=tuple(kicks[k])) for k in range(4)]
+    mix = Server(lambda r: 1, OracleSystem, budget_bytes=3, max_active=3, keep_orbitals=True).run(reqs)
+    for r, o in zip(reqs, mix):
+        (a,) = Server(lambda r: 1, OracleSystem, budget_bytes=3, max_active=1, keep_orbitals=True).run([r])
+        assert o.error is None and a.error is None
+        assert len(o.energy) == r.steps
+        assert np.array_equal(a.orbitals, o.orbitals) and a.energy == o.energy
+    # different requests really differ (the comparison above is not vacuous)
+    assert not np.allclose(mix[0].orbitals, mix[1].orbitals)
