@@ -6,6 +6,7 @@ run are admitted as soon as memory frees up, oversized and failing requests are
 reported without stopping the others, and every request gets its own results
 back whatever the mix (a stand-in that steps an oracle model per request).
 """
+import os
 import threading
 import time
 
@@ -159,3 +160,63 @@ def test_results_are_the_same_alone_and_in_the_mix():
         assert np.array_equal(a.orbitals, o.orbitals) and a.energy == o.energy
     # different requests really differ (the comparison above is not vacuous)
     assert not np.allclose(mix[0].orbitals, mix[1].orbitals)
+
+
+def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
+    """The CUDA backend's glue and the command line, with torch's stream calls and the
+    System class replaced by host stand-ins (pt_workspace_size and the basis listing are
+    host-only calls of the real library)."""
+    import contextlib
+    import json
+    import torch
+    import paper_1905_01348_gb300 as pkg
+    import paper_1905_01348_gb300.system as system_mod
+    from paper_1905_01348_gb300 import build as b
+    from paper_1905_01348_gb300 import serve
+    if not os.path.exists(pkg._native.LIB_PATH):
+        b.build()
+
+    class FakeStream:
+        def __init__(self, device=None):
+            self.cuda_stream = 0
+
+    made = []
+
+    class FakeSystem:
+        def __init__(self, params, psi0, device="cuda:0", stream=None):
+            assert isinstance(stream, FakeStream) and device == "cuda:0"
+            assert psi0.shape[0] == params["n_orb"]
+            self.params, self.psi0, self.k = params, psi0, 0
+            made.append(self)
+
+        def step(self):
+            self.k += 1
+            return 0, {"energy": -1.0 * self.k, "dipole": np.zeros(3), "scf_iters": 1}
+
+        def orbitals(self):
+            return self.psi0
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(system_mod, "System", FakeSystem)
+
+    serve.main(["--batched", "--budget-gb", "1000", "--max-active", "4", "--check-alone"])
+    res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert res["mode"] == "batched" and res["requests"] == 24 and res["completed"] == 24
+    assert res["steps"] == 24 * 20 and res["peak_active"] <= 4
+    assert res["alone_vs_mix"] == {"max_orbital_diff": 0.0, "max_energy_diff_ha": 0.0}
+    kicks = syn.batched_kicks(24, seed=1)
+    firsts = made[:24]
+    assert sorted(tuple(s.params["kick"]) for s in firsts) == sorted(tuple(k) for k in kicks)
+    assert sum(s.params["n_orb"] == 16 for s in firsts) == 12
+    assert all(s.params["precision"] == "mixed" and s.params["fock_mode"] == "ace" for s in firsts)
+
+    made.clear()
+    serve.main(["--requests", "5", "--rate", "50", "--steps-max", "6", "--workloads", "si8,si64",
+                "--budget-gb", "1000"])
+    res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert res["mode"] == "poisson" and res["completed"] == 5 and res["step_latency_ms"]["p99"] is not None
