@@ -1,7 +1,7 @@
 """ORACLE (test infrastructure only): planewave discretisation of a periodic cell.
 
 The paper works at the Gamma point with a planewave basis cut off at
-|G|^2/2 <= Ecut (Sec. 3.1, Sec. 4: "kinetic energy cutoff ... 10 Hartree").
+|G|^2/2 <= Ecut (Sec. 3.1; Sec. 4 sets the cutoff to 10 Ha).
 Orbitals are stored as basis coefficients c(G) with
 
     psi(r) = Omega^{-1/2} sum_G c(G) exp(i G.r),      sum_G |c(G)|^2 = <psi|psi>,

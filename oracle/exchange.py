@@ -6,9 +6,9 @@ Eq. 3 applies the exchange operator to an orbital psi_j as
 
 one Poisson-like solve per pair (i, j), N_e^2 of them (Sec. 2; Alg. 2 loops
 over i and j). The kernel is the screened interaction of the range-separated
-hybrid, with the mixing fraction alpha of Sec. 2 ("kernel -alpha P(r,r') K")
-kept in front. Reading: Eq. 3 drops alpha; it is restored here, as the
-operator kernel of Sec. 2 has it.
+hybrid, with the mixing fraction alpha of Sec. 2 (whose operator kernel is
+-alpha P(r,r') K(r,r')) kept in front. Reading: Eq. 3 drops alpha; it is
+restored here, as the operator kernel of Sec. 2 has it.
 
 The screened Coulomb kernel is K(r) = erfc(w r)/r, whose Fourier transform is
 
