@@ -60,7 +60,7 @@ def test_admission_by_footprint_and_slots():
     assert srv.peak_bytes <= 100 and srv.peak_active <= 3 and SleepSystem.open_peak <= 3
     by = {o.rid: o for o in outs}
     # 0 and 1 start at once; 2 must wait for memory, and 3, 4 queue behind it (arrival order)
-    assert by[0].admitted_s < 0.005 and by[1].admitted_s < 0.005
+    assert by[0].admitted_s < 0.05 and by[1].admitted_s < 0.05
     assert by[2].admitted_s >= min(by[0].finished_s, by[1].finished_s) - 1e-6
     assert by[3].admitted_s >= by[2].admitted_s and by[4].admitted_s >= by[3].admitted_s
     # 2 was admitted when 0 finished, while 1 was still running: continuous admission
