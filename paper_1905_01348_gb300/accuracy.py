@@ -9,8 +9,11 @@ so the mixed run's error is reported beside the FP64 run's own error at the
 same tolerance. Per step: total-energy difference per atom and dipole
 difference (max over the three components); at the end the subspace defect
 n_orb - ||Psi_a^H Psi_b||_F^2 (zero when the occupied subspaces agree).
-The start state (orthonormalisation and relaxation) is computed by each run
-itself. Prints one JSON object.
+With `--mixed-tight-tol` a fourth run takes mixed precision to that tolerance
+and is compared with the tight FP64 run: with both iterations converged far
+below the paper's 1e-6, what remains is the precision error alone. The start
+state (orthonormalisation and relaxation) is computed by each run itself.
+Prints one JSON object.
 
     python -m paper_1905_01348_gb300.accuracy --workload si8 --steps 20
 """
@@ -28,6 +31,8 @@ def main(argv=None) -> None:
     ap.add_argument("--fock-mode", default="ace", choices=["ace", "exact"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tight-tol", type=float, default=1e-9)
+    ap.add_argument("--mixed-tight-tol", type=float, default=0.0,
+                    help="also run mixed precision at this SCF tolerance and compare it with the tight FP64 run")
     ap.add_argument("--fock-grid", type=int, default=0,
                     help="also run mixed precision with the pair FFTs on this cubic grid and report the aliasing error")
     args = ap.parse_args(argv)
@@ -46,6 +51,8 @@ def main(argv=None) -> None:
     runs = {}
     cases = [("fp64", "fp64", base["scf_tol"], None), ("mixed", "mixed", base["scf_tol"], None),
              ("fp64_tight", "fp64", args.tight_tol, None)]
+    if args.mixed_tight_tol > 0:
+        cases.append(("mixed_tight", "mixed", args.mixed_tight_tol, None))
     if args.fock_grid:
         cases.append(("mixed_fock", "mixed", base["scf_tol"], (args.fock_grid,) * 3))
     for name, prec, tol, fock in cases:
@@ -77,6 +84,8 @@ def main(argv=None) -> None:
            "mixed_vs_fp64": compare(runs["mixed"], runs["fp64"]),
            "mixed_vs_fp64_tight": compare(runs["mixed"], ref),
            "fp64_vs_fp64_tight": compare(runs["fp64"], ref),
+           **({"mixed_tight_vs_fp64_tight": compare(runs["mixed_tight"], ref), "mixed_tight_tol": args.mixed_tight_tol}
+              if args.mixed_tight_tol > 0 else {}),
            **({"mixed_fock_vs_mixed": compare(runs["mixed_fock"], runs["mixed"]),
                "mixed_fock_vs_fp64_tight": compare(runs["mixed_fock"], ref), "fock_grid": args.fock_grid}
               if args.fock_grid else {}),
