@@ -23,7 +23,21 @@
 #include "kernels.h"
 #include "fft.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using pt::Grid3;
+
+namespace {
+// Named range around one phase of a step for profilers (NVTX; header-only, a no-op
+// unless a tool is attached). Phases follow the timing rows of the paper's Table 1:
+// H Psi, exchange / ACE, residual, Anderson mixing, density, orthonormalisation.
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -638,6 +652,7 @@ static pt_status read_status(pt_system* sys, int* h) {
 
 // dst = src L^{-H}, L L^H = src^H src  (Sec. 3.4)
 static pt_status orthonormalize(pt_system* sys, const double2* src, double2* dst) {
+  Phase phase_("orthonormalize");
   const int ne = sys->ne, npw = sys->npw;
   PT_TRY(gemm<double>(sys, pt::OP_H, pt::OP_N, ne, ne, npw, kOne, src, npw, src, npw, kZero, sys->S, ne,
                       pt::GEMM_HERM));
@@ -685,6 +700,7 @@ static pt_status ace_from_w(pt_system* sys) {
 
 // exchange data of psi (psi_r current): wg = V_X psi, then its ACE data
 static pt_status exchange_data(pt_system* sys) {
+  Phase phase_("exchange + ACE build");
   PT_TRY(exchange_sym(sys, sys->psi, sys->wg, 0));
   return ace_from_w(sys);
 }
@@ -725,6 +741,7 @@ static pt_status observables(pt_system* sys) {
 
 // relaxation of the start state: psi <- orth(psi - tau P (H_loc psi - psi S))
 static pt_status relax(pt_system* sys) {
+  Phase phase_("relax start state");
   const int ne = sys->ne, npw = sys->npw;
   const long n = (long)npw * ne;
   if (sys->p.relax_iters > 0) {
@@ -747,6 +764,7 @@ static pt_status relax(pt_system* sys) {
 }
 
 static pt_status state_from_psi(pt_system* sys) {
+  Phase phase_("new state");
   PT_TRY(real_orbitals(sys, sys->psi));
   sys->psi_r_current = true;
   PT_TRY(exchange_data(sys));
@@ -777,6 +795,7 @@ static pt_status set_kinetic(pt_system* sys, int64_t n) { return set_kinetic_t(s
 
 // one PT-CN step (Eq. 5, Alg. 1)
 static pt_status cn_step(pt_system* sys, pt_step_info* info) {
+  Phase phase_("PT-CN step");
   const int ne = sys->ne, npw = sys->npw;
   const long n = (long)npw * ne;
   const double hdt = 0.5 * sys->p.dt;
@@ -807,43 +826,55 @@ static pt_status cn_step(pt_system* sys, pt_step_info* info) {
   int it = 0;
   double drho = 0.0;
   for (it = 1; it <= niter; ++it) {
-    PT_TRY(local_potential(sys));
-    PT_TRY(apply_local_scf(sys, sys->psi_f, sys->hpsi));
-    if (sys->p.alpha != 0.0) {
-      if (sys->p.fock_mode == PT_FOCK_EXACT) PT_TRY(exchange_sym(sys, sys->psi_f, sys->hpsi, 1));
-      else PT_TRY(ace_apply(sys, sys->psi_f, ne, sys->hpsi));
-    }
-    PT_TRY(projection(sys, sys->psi_f, sys->hpsi));
-    PT_CK(pt::pt_residual(sys->psi_f, sys->hpsi, sys->psi_half, hdt, sys->rbuf, n, sys->part, sys->red + 0, sys->s));
-    // Anderson (per band)
-    int newslot = -1;
-    if (have_prev && m > 0) {
-      if (sys->and_count < m) {
-        newslot = sys->and_count;
-        sys->and_count++;
-      } else {
-        newslot = sys->and_order.front();
-        sys->and_order.erase(sys->and_order.begin());
+    Phase iter_("SCF iteration");
+    {
+      Phase p_("H Psi");
+      PT_TRY(local_potential(sys));
+      PT_TRY(apply_local_scf(sys, sys->psi_f, sys->hpsi));
+      if (sys->p.alpha != 0.0) {
+        Phase x_(sys->p.fock_mode == PT_FOCK_EXACT ? "exchange" : "ACE apply");
+        if (sys->p.fock_mode == PT_FOCK_EXACT) PT_TRY(exchange_sym(sys, sys->psi_f, sys->hpsi, 1));
+        else PT_TRY(ace_apply(sys, sys->psi_f, ne, sys->hpsi));
       }
-      sys->and_order.push_back(newslot);
     }
-    const size_t hs = sys->mixed ? sizeof(float2) : sizeof(double2);
-    PT_CK(pt::anderson_push(sys->psi_f, sys->rbuf, sys->xprev, sys->rprev,
-                            sys->dX + (newslot >= 0 ? newslot : 0) * stride * hs,
-                            sys->dR + (newslot >= 0 ? newslot : 0) * stride * hs, n, newslot >= 0 ? 1 : 0,
-                            sys->mixed ? 1 : 0, sys->s));
-    have_prev = true;
-    pt::SlotList sl{};
-    sl.k = (int)sys->and_order.size();
-    for (int q = 0; q < sl.k; ++q) sl.s[q] = sys->and_order[q];
-    if (sl.k > 0) {
-      PT_CK(pt::anderson_dots(sys->dR, stride, sl, newslot, sys->rbuf, npw, ne, m, sys->gram, sys->rhs,
+    {
+      Phase p_("PT residual");
+      PT_TRY(projection(sys, sys->psi_f, sys->hpsi));
+      PT_CK(pt::pt_residual(sys->psi_f, sys->hpsi, sys->psi_half, hdt, sys->rbuf, n, sys->part, sys->red + 0, sys->s));
+    }
+    // Anderson (per band)
+    {
+      Phase and_("Anderson");
+      int newslot = -1;
+      if (have_prev && m > 0) {
+        if (sys->and_count < m) {
+          newslot = sys->and_count;
+          sys->and_count++;
+        } else {
+          newslot = sys->and_order.front();
+          sys->and_order.erase(sys->and_order.begin());
+        }
+        sys->and_order.push_back(newslot);
+      }
+      const size_t hs = sys->mixed ? sizeof(float2) : sizeof(double2);
+      PT_CK(pt::anderson_push(sys->psi_f, sys->rbuf, sys->xprev, sys->rprev,
+                              sys->dX + (newslot >= 0 ? newslot : 0) * stride * hs,
+                              sys->dR + (newslot >= 0 ? newslot : 0) * stride * hs, n, newslot >= 0 ? 1 : 0,
                               sys->mixed ? 1 : 0, sys->s));
-      PT_CK(pt::anderson_solve(sys->gram, sys->rhs, sl, m, ne, sys->gamma, sys->s));
+      have_prev = true;
+      pt::SlotList sl{};
+      sl.k = (int)sys->and_order.size();
+      for (int q = 0; q < sl.k; ++q) sl.s[q] = sys->and_order[q];
+      if (sl.k > 0) {
+        PT_CK(pt::anderson_dots(sys->dR, stride, sl, newslot, sys->rbuf, npw, ne, m, sys->gram, sys->rhs,
+                                sys->mixed ? 1 : 0, sys->s));
+        PT_CK(pt::anderson_solve(sys->gram, sys->rhs, sl, m, ne, sys->gamma, sys->s));
+      }
+      PT_CK(pt::anderson_update(sys->psi_f, sys->rbuf, sys->dX, sys->dR, stride, sl, sys->gamma, std::max(m, 1), npw, n,
+                                sys->p.anderson_beta, sys->mixed ? 1 : 0, sys->s));
     }
-    PT_CK(pt::anderson_update(sys->psi_f, sys->rbuf, sys->dX, sys->dR, stride, sl, sys->gamma, std::max(m, 1), npw, n,
-                              sys->p.anderson_beta, sys->mixed ? 1 : 0, sys->s));
     // new density and its change
+    Phase rho_("density");
     PT_TRY(real_orbitals_scf(sys, sys->psi_f));
     PT_TRY(density_scf(sys, sys->rho2));
     PT_CK(pt::rho_change(sys->rho2, sys->rho, sys->N, sys->part, sys->red + 1, sys->s));
@@ -896,6 +927,7 @@ static pt_status h_of_self(pt_system* sys, const double2* X, double2* out, doubl
 // t_n + dt; Psi_{n+1} = Psi_n + dt/6 (k_1 + 2 k_2 + 2 k_3 + k_4). k_1 uses the stored
 // exchange of Psi_n; the other stages evaluate V_X of their own orbitals.
 static pt_status rk4_step(pt_system* sys, pt_step_info* info) {
+  Phase phase_("RK4 step");
   const long n = (long)sys->npw * sys->ne;
   const double dt = sys->p.dt;
   const double t = (double)sys->n_step * dt;
