@@ -1,5 +1,7 @@
-"""The accuracy tool's bookkeeping on the host, with a stand-in System (the
-library's host-only calls are real; no device work)."""
+"""The accuracy and trajectory tools' bookkeeping on the host, with stand-in
+systems (the library's host-only calls are real; no device work): the accuracy
+comparisons, the per-step log, and a checkpoint written mid-run and resumed,
+whose log continues the uninterrupted one line for line."""
 import json
 import os
 
@@ -53,3 +55,47 @@ def test_accuracy_tool_reports_every_comparison(pkg, monkeypatch, capsys):
         3 * (1e-7 + 1e-8 - 1e-9) / n_atoms)
     assert out["mixed_vs_fp64"]["max_dipole_diff_au"] == pytest.approx(3 * 1e-7)
     assert set(out["scf_iters"]) == {"fp64", "mixed", "fp64_tight", "mixed_tight"}
+
+
+class FakeStateSystem:
+    """Deterministic in the step index; state = (psi, w, step) as pt_get_state gives it."""
+
+    def __init__(self, params, psi0, device="cuda:0", stream=None):
+        self.psi = np.array(psi0, dtype=np.complex128)
+        self.w = -0.5 * self.psi
+        self.k = 0
+
+    def step(self):
+        self.k += 1
+        self.psi = self.psi * np.exp(-0.01j * self.k)
+        self.w = -0.5 * self.psi
+        return 0, {"energy": -10.0 + 1e-3 * self.k, "dipole": np.array([self.k, 0.0, 0.0]), "scf_iters": 20 + self.k,
+                   "converged": True, "resid_norm": 1e-6, "drho": 1e-7}
+
+    def get_state(self):
+        return self.psi.copy(), self.w.copy(), self.k
+
+    def set_state(self, psi, w, step):
+        self.psi, self.w, self.k = psi.copy(), w.copy(), step
+
+    def close(self):
+        pass
+
+
+def test_trajectory_log_and_checkpoint_resume(pkg, monkeypatch, tmp_path):
+    from paper_1905_01348_gb300 import trajectory
+    monkeypatch.setattr(pkg, "System", FakeStateSystem)
+    full, part, ck = tmp_path / "full.jsonl", tmp_path / "part.jsonl", tmp_path / "state.npz"
+    assert trajectory.main(["--workload", "si8", "--steps", "6", "--out", str(full)]) == 0
+    assert trajectory.main(["--workload", "si8", "--steps", "4", "--out", str(part), "--checkpoint", str(ck),
+                            "--checkpoint-every", "2"]) == 0
+    psi, w, step = trajectory.load_checkpoint(str(ck))
+    assert step == 4 and np.array_equal(w, -0.5 * psi)
+    assert trajectory.main(["--workload", "si8", "--steps", "2", "--out", str(part), "--resume", str(ck)]) == 0
+    a = [json.loads(l) for l in full.read_text().splitlines()]
+    b = [json.loads(l) for l in part.read_text().splitlines()]
+    assert [r["step"] for r in b] == [1, 2, 3, 4, 5, 6]
+    for ra, rb in zip(a, b):
+        for key in ("step", "time_au", "energy", "dipole", "scf_iters", "converged"):
+            assert ra[key] == rb[key], key
+    assert a[-1]["time_fs"] == pytest.approx(6 * 2.07 / 41.341374575751)
