@@ -175,10 +175,6 @@ static int round_threads(int t) {
   return std::max(64, std::min(1024, t));
 }
 
-size_t fock_scratch_elems(const FockPlan& plan, Grid3 g) {
-  return (size_t)plan.tiles_per_launch * kTileMax * kTileMax * (size_t)g.N();
-}
-
 template <typename T>
 cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
                        Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s) {
