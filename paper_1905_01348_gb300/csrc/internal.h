@@ -120,7 +120,7 @@ struct FockPlan {
 template <typename T>
 cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
                        Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s);
-// FP32 cubic fast path (fock_fast.cu): n0 == n1 == n2 in {32, 64, 96}.
+// FP32 cubic fast path (fock_fast.cu): n0 == n1 == n2 in {32, 48, 64, 96}.
 bool fock_fast_supported(Grid3 g);
 cudaError_t fock_pairs_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, Grid3 g,
                             const float* khat_t, void* scratch, const float2* tw_L, cudaStream_t s);
