@@ -152,10 +152,6 @@ cudaError_t cholesky(double2* A, int n, int* d_status, cudaStream_t s);
 // Linv = L^{-1} for lower-triangular L (n x n, column-major).
 cudaError_t tri_inverse(const double2* L, double2* Linv, int n, cudaStream_t s);
 
-// ---- elementwise / reductions (ptcn.cu) -------------------------------------
-// Deterministic sums: partial sums per block then a single-block final pass.
-cudaError_t reduce_norm2(const double2* x, long n, double* partials, int npart, double* out, cudaStream_t s);
-
 std::string cuda_msg(cudaError_t e);
 
 // One-time per-device setup (kernel attributes, occupancy queries): bit d of `mask`

@@ -554,18 +554,6 @@ cudaError_t hartree_factor(double* f, Grid3 g, const double* cell, cudaStream_t 
   return cudaGetLastError();
 }
 
-__global__ void k_copy_scaled(const double2* __restrict__ a, double2* __restrict__ b, long n, double s) {
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
-    const double2 v = a[t];
-    b[t] = make_double2(s * v.x, s * v.y);
-  }
-}
-
-cudaError_t copy_scaled(const double2* a, double2* b, long n, double sc, cudaStream_t s) {
-  k_copy_scaled<<<nblk(n, 256), 256, 0, s>>>(a, b, n, sc); launched();
-  return cudaGetLastError();
-}
-
 }  // namespace pt
 
 namespace pt {

@@ -41,7 +41,6 @@ cudaError_t rho_change(const double* a, const double* b, long N, double* part, d
 cudaError_t energy_sums(const double* rho, const double* vion, const double* vh, int use_h, Grid3 g, const double* cell,
                         const double2* c, const double* kin, int npw, int ne, const double2* negM, double* part,
                         double* out8, cudaStream_t s);
-cudaError_t copy_scaled(const double2* a, double2* b, long n, double sc, cudaStream_t s);
 cudaError_t axpy(double2 a, const double2* x, double2* y, long n, cudaStream_t s);
 cudaError_t diff_to_complex(const double* a, const double* b, double2* buf, long N, cudaStream_t s);
 cudaError_t add_real(const double2* buf, double* a, long N, cudaStream_t s);
