@@ -108,6 +108,26 @@ def test_ptcn_steps_fp64(pkg, fock_mode):
     s.close()
 
 
+def test_si8_trajectory_fp64(pkg):
+    """Si8 workload (32^3 grid, 16 orbitals, ACE per step), FP64, 10 PT-CN steps with a
+    fixed number of SCF iterations, against the oracle's trajectory step by step. The
+    bound is the FP64 target of 1e-10 for energy and dipole; the orbitals get 1e-9: their
+    rounding differences pass through ten fixed-point solves, and an indexing or sign
+    error would show at order one."""
+    w = syn.si_workload("si8", relax_iters=10, scf_fixed_iters=6)
+    model, C0 = make(w)
+    st = model.init_state(C0)
+    s = pkg.System(w, C0)
+    for _ in range(10):
+        st, info_o = model.step(st)
+        status, info_g = s.step()
+        assert rel(s.orbitals().T, st.Psi) < 1e-9
+        assert abs(info_g["energy"] - info_o.energy) < 1e-10 * abs(info_o.energy)
+        assert np.max(np.abs(info_g["dipole"] - info_o.dipole)) < 1e-10 * np.max(np.abs(info_o.dipole))
+        assert abs(info_g["time"] - st.step * w["dt"]) < 1e-12
+    s.close()
+
+
 def test_ptcn_tolerance_mode_si8(pkg):
     """Si8 workload, SCF run to the paper's 1e-6 density tolerance: same iteration counts and observables."""
     w = syn.si_workload("si8", relax_iters=10)
