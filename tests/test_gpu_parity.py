@@ -128,6 +128,28 @@ def test_si8_trajectory_fp64(pkg):
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_single_orbital(pkg, precision, tol):
+    """The degenerate case of one orbital: a single diagonal pair (tile of one orbital),
+    1 x 1 Gram and Cholesky, one Anderson band; the FP64 generic path on a non-cubic grid
+    and the FP32 cubic path on the Si8 cell."""
+    if precision == "fp64":
+        w = dict(NONCUBIC, n_orb=1, fock_mode="exact", scf_fixed_iters=4, relax_iters=2, dt=1.0)
+    else:
+        w = syn.si_workload("si8", n_orb=1, relax_iters=2, precision="mixed", fock_mode="ace", scf_fixed_iters=4,
+                            dt=1.0)
+    model, C0 = make(w, seed=8)
+    st = model.init_state(C0)
+    s = pkg.System(w, C0)
+    assert rel(s.exchange().cpu().numpy().T, st.W) < (1e-10 if precision == "fp64" else 2e-5)
+    for _ in range(2):
+        st, info_o = model.step(st)
+        status, info_g = s.step()
+        assert rel(s.orbitals().T, st.Psi) < tol
+        assert abs(info_g["energy"] - info_o.energy) < tol * abs(info_o.energy)
+    s.close()
+
+
 def test_ptcn_tolerance_mode_si8(pkg):
     """Si8 workload, SCF run to the paper's 1e-6 density tolerance: same iteration counts and observables."""
     w = syn.si_workload("si8", relax_iters=10)
