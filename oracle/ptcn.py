@@ -62,7 +62,9 @@ Readings (the paper is silent on these details):
       rho_mix <- rho_mix + F^{-1}[ b |G|^2 / (|G|^2 + q0^2) F[rho(Psi) - rho_mix] ],
   rho_mix starting at rho(Psi_0) (b = relax_mix, q0 = relax_q0). Without
   the mixing the long-wavelength Hartree response (4 pi / |G|^2, growing with
-  the cell) makes the descent unstable in the 3x3x3 supercell.
+  the cell) makes the descent unstable in the 3x3x3 supercell. Pinned by its
+  fixed point (tests/test_oracle_relax.py): the lowest eigen-subspace of the
+  dense H for a linear H, the self-consistent aufbau state with Hartree + LDA.
 """
 from __future__ import annotations
 
