@@ -53,8 +53,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fock-grid", type=int, default=0,
                     help="edge of a cubic Fock grid for the pair FFTs (0: the workload grid, the headline)")
-    ap.add_argument("--ref-sample-s", type=float, default=8.0,
+    ap.add_argument("--ref-sample-s", type=float, default=5.0,
                     help="host seconds of oracle work per reference-arm step")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the FP64 leg (0: no FP64 leg); it starts from the mixed run's state")
+    ap.add_argument("--fp64-warmup", type=int, default=1)
     return ap.parse_args()
 
 
@@ -104,6 +107,19 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# FP64 peak of GB300: 1.25 TFLOP/s (the pool's nominal figure; a register-FMA probe of this
+# library's own measured 1.19 TFLOP/s, DMMA 1.05). FP64 runs at 1/64 of the FP32 rate here.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def pair_fft_flops(n) -> float:
+    """Algorithmic FLOPs per unordered pair of the FP64 pair pipeline: one forward and
+    one inverse complex 3D FFT, 5 N log2 N each (the usual radix-2 count)."""
+    import math
+    N = int(n[0]) * int(n[1]) * int(n[2])
+    return 2.0 * 5.0 * N * math.log2(N)
 
 
 def live_fraction(basis_idx, n) -> float:
@@ -235,16 +251,21 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    res = []
+    res, wall = [], []
     for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         r = cpu_oracle_pairs_per_s(args.workload, budget_s=args.ref_sample_s, seed=k)
         if k >= args.warmup:
             res.append(r)
+            wall.append(time.perf_counter() - t0)
     value = statistics.mean(r["value"] for r in res)
     n_orb = {"si8": 16, "si64": 128, "si216": 432}[args.workload]
-    ms_per_step = pairs_per_exchange(n_orb) / value * 1e3
+    # a reference step is one bounded oracle sample; ms_per_step is its measured wall time
+    ms_per_step = 1e3 * sum(wall) / len(wall)
     line = {"impl": "reference", "metric": metric_name(args.workload, args.precision), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "step_definition": "one bounded sample of the oracle's pair loop (not a PT-CN step)",
+            "extrapolated_ms_per_exchange": pairs_per_exchange(n_orb) / value * 1e3,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, args.precision, args.gpus, args.fock_grid),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res[0]["cores"], "kind": "oracle",
@@ -252,6 +273,53 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+def fp64_leg(args, w_mixed: dict, C0, state, dev) -> dict:
+    """The FP64 GPU path on the same state: an FP64 system is created (no relaxation), given
+    the mixed run's last state (Psi_n, W_n, n) through pt_set_state, stepped fp64_warmup
+    times untimed and fp64_steps times between CUDA events on its stream. Its pair
+    pipeline is FP64-ALU bound: the roofline is FLOPs of the pair FFTs against the FP64 peak."""
+    import torch
+    import paper_1905_01348_gb300 as pkg
+    w = dict(w_mixed, precision="fp64", relax_iters=0)
+    sysg = pkg.System(w, C0, device=str(dev))
+    psi, wv, step = state
+    sysg.set_state(psi, wv, step)
+    stream = sysg.stream
+    pkg.pt_set_timing(sysg.handle, True)
+    for _ in range(args.fp64_warmup):
+        sysg.step()
+    pkg.pt_get_timing(sysg.handle, reset=True)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps + 1)]
+    ev[0].record(stream)
+    iters = []
+    for k in range(args.fp64_steps):
+        st, info = sysg.step()
+        iters.append(info["scf_iters"])
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.fp64_steps)]
+    pair_ms, pair_count, groups = pkg.pt_get_timing(sysg.handle, reset=True)
+    sysg.close()
+    del sysg
+    torch.cuda.empty_cache()
+    pairs = pairs_per_exchange(w["n_orb"])
+    flops_pair = pair_fft_flops(w["n"])
+    achieved = flops_pair * pair_count / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
+    return {"pairs_per_s": pairs * args.fp64_steps / (t_ms / 1e3), "ms_per_step": t_ms / args.fp64_steps,
+            "wall_s_per_fs": t_ms / args.fp64_steps * STEPS_PER_FS / 1e3, "steps": args.fp64_steps,
+            "warmup": args.fp64_warmup, "step_ms": step_ms, "scf_iters": iters,
+            "start": "the mixed run's last state through pt_set_state (same Psi_n, W_n)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                         "kernel": "FP64 pair pipeline (fock.cu pair kernels and 3D FFT passes)",
+                         "alg_flops_per_pair": flops_pair, "pair_pipeline_ms": pair_ms,
+                         "pairs_per_s_in_pipeline": pair_count / (pair_ms / 1e3) if pair_ms > 0 else None,
+                         "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}}
 
 
 # ---------------------------------------------------------------------------
@@ -379,6 +447,14 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_pairs_per_s(args.workload)
 
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0 and not args.fock_grid:
+        state = sysg.get_state()
+        sysg.close()
+        del sysg
+        torch.cuda.empty_cache()
+        sysg = None
+        fp64 = fp64_leg(args, w, C0, state, dev)
 
     if rank == 0:
         line = {
@@ -395,8 +471,12 @@ def run_gpu(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
         }
+        if fp64 is not None:
+            line["fp64"] = fp64
+            line["speedup_mixed_over_fp64"] = value / fp64["pairs_per_s"]
         print(json.dumps(line), flush=True)
-    sysg.close()
+    if sysg is not None:
+        sysg.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -225,6 +225,52 @@ static int pair_g2_reach(const pt_params* p) {
   return 2 * m;
 }
 
+// Screened kernel K(G) = 4 pi (1 - exp(-G^2 / (4 w^2))) / G^2, K(0) = pi / w^2 (its limit),
+// on the grid g in the pair-intermediate layout [i2][i0][i1], scaled by -alpha / N (the
+// inverse-FFT factor) so that the pair kernels multiply by it directly (Eq. 3).
+static std::vector<double> khat_table(const pt_params* p, Grid3 g) {
+  const int n0 = g.n0, n1 = g.n1, n2 = g.n2;
+  const double w2 = p->omega * p->omega;
+  const double scale = -p->alpha / (double)g.N();
+  std::vector<double> kt((size_t)g.N());
+  for (int i2 = 0; i2 < n2; ++i2)
+    for (int i0 = 0; i0 < n0; ++i0)
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const double g0 = 2.0 * M_PI * freq(i0, n0) / p->cell[0];
+        const double g1 = 2.0 * M_PI * freq(i1, n1) / p->cell[1];
+        const double gz = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
+        const double gg = g0 * g0 + g1 * g1 + gz * gz;
+        const double k = gg > 0.0 ? 4.0 * M_PI * (-std::expm1(-gg / (4.0 * w2))) / gg : M_PI / w2;
+        kt[((size_t)i2 * n0 + i0) * n1 + i1] = scale * k;
+      }
+  return kt;
+}
+
+// Uploads the twiddle tables (FP64 and FP32) and the kernel table of grid g in the
+// exchange precision; synchronises the stream before the host vectors go away.
+static cudaError_t upload_fft_tables(const pt_params* p, Grid3 g, bool mixed, double2* tw64, float2* tw32,
+                                     double* khat64, float* khat32, cudaStream_t s) {
+  std::vector<double2> tw(pt::kTwiddleTotal);
+  pt::twiddle_host(tw.data());
+  std::vector<float2> twf(pt::kTwiddleTotal);
+  for (int k = 0; k < pt::kTwiddleTotal; ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+  const std::vector<double> kt = khat_table(p, g);
+  std::vector<float> kf;
+  cudaError_t e = cudaMemcpyAsync(tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tw32, twf.data(), sizeof(float2) * twf.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (mixed) {
+      kf.resize(kt.size());
+      for (size_t k = 0; k < kt.size(); ++k) kf[k] = (float)kt[k];
+      e = cudaMemcpyAsync(khat32, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice, s);
+    } else {
+      e = cudaMemcpyAsync(khat64, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice, s);
+    }
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  return e != cudaSuccess ? e : e2;
+}
+
 static int choose_tile(const pt_params* p) {
   if (p->pair_tile > 0) return p->pair_tile;
   return std::min(pt::kTileMax, p->n_orb);
@@ -1031,35 +1077,9 @@ static size_t static_layout(pt_system* t, const pt_params* p, int npw, uintptr_t
 static pt_status exchange_static_body(pt_system* t, const pt_params* p, const std::vector<int>& idx,
                                       const double2* d_psi, double2* d_w) {
   pt_system* sys = t;   // for PT_CK messages
-  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
-  std::vector<double2> tw(pt::kTwiddleTotal);
-  pt::twiddle_host(tw.data());
-  std::vector<float2> tw32(pt::kTwiddleTotal);
-  for (int k = 0; k < pt::kTwiddleTotal; ++k) tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
-  const double w2 = p->omega * p->omega;
-  std::vector<double> kt((size_t)t->N);
-  for (int i2 = 0; i2 < n2; ++i2)
-    for (int i0 = 0; i0 < n0; ++i0)
-      for (int i1 = 0; i1 < n1; ++i1) {
-        const double g0 = 2.0 * M_PI * freq(i0, n0) / p->cell[0];
-        const double g1 = 2.0 * M_PI * freq(i1, n1) / p->cell[1];
-        const double gz = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
-        const double gg = g0 * g0 + g1 * g1 + gz * gz;
-        const double k = gg > 0.0 ? 4.0 * M_PI * (-std::expm1(-gg / (4.0 * w2))) / gg : M_PI / w2;
-        kt[((size_t)i2 * n0 + i0) * n1 + i1] = -p->alpha * k / (double)t->N;
-      }
   cudaStream_t s = t->s;
   PT_CK(cudaMemcpyAsync(t->basis, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
-  PT_CK(cudaMemcpyAsync(t->tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
-  PT_CK(cudaMemcpyAsync(t->tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice, s));
-  if (t->mixed) {
-    std::vector<float> kf(kt.size());
-    for (size_t k = 0; k < kt.size(); ++k) kf[k] = (float)kt[k];
-    PT_CK(cudaMemcpyAsync(t->khat32, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaStreamSynchronize(s));
-  } else {
-    PT_CK(cudaMemcpyAsync(t->khat64, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice, s));
-  }
+  PT_CK(upload_fft_tables(p, t->g, t->mixed, t->tw64, t->tw32, t->khat64, t->khat32, s));
   pt::PairTile* tiles = nullptr;
   int *lf = nullptr, *lc = nullptr, nl = 0;
   const int nt = pt::fock_build_tiles(t->ne, 0, t->plan_sym.tile, 1, t->plan_sym.tiles_per_launch, &tiles, &lf, &lc, &nl);
@@ -1178,40 +1198,13 @@ static pt_status init_body(pt_system* sys, const double* psi0_host) {
       kin[k++] = 0.5 * (gk0 * gk0 + gk1 * gk1 + gk2 * gk2);
     }
   }
-  std::vector<double2> tw(pt::kTwiddleTotal);
-  pt::twiddle_host(tw.data());
-  std::vector<float2> tw32(pt::kTwiddleTotal);
-  for (int t = 0; t < pt::kTwiddleTotal; ++t) tw32[t] = make_float2((float)tw[t].x, (float)tw[t].y);
-  // screened kernel on the Fock grid in the pair-intermediate layout [i2][i0][i1],
-  // scaled by -alpha / N_f (the inverse-FFT factor)
-  const int n0 = sys->gf.n0, n1 = sys->gf.n1, n2 = sys->gf.n2;
-  const double w2 = p->omega * p->omega;
-  std::vector<double> kt((size_t)sys->Nf);
-  for (int i2 = 0; i2 < n2; ++i2)
-    for (int i0 = 0; i0 < n0; ++i0)
-      for (int i1 = 0; i1 < n1; ++i1) {
-        const double g0 = 2.0 * M_PI * freq(i0, n0) / p->cell[0];
-        const double g1 = 2.0 * M_PI * freq(i1, n1) / p->cell[1];
-        const double gz = 2.0 * M_PI * freq(i2, n2) / p->cell[2];
-        const double gg = g0 * g0 + g1 * g1 + gz * gz;
-        const double k = gg > 0.0 ? 4.0 * M_PI * (-std::expm1(-gg / (4.0 * w2))) / gg : M_PI / w2;
-        kt[((size_t)i2 * n0 + i0) * n1 + i1] = -p->alpha * k / (double)sys->Nf;
-      }
   cudaStream_t s = sys->s;
   PT_CK(cudaMemcpyAsync(sys->basis, idx.data(), sizeof(int) * npw, cudaMemcpyHostToDevice, s));
   PT_CK(cudaMemcpyAsync(sys->kin, kin.data(), sizeof(double) * npw, cudaMemcpyHostToDevice, s));
   PT_CK(cudaMemcpyAsync(sys->gk3, gk3.data(), sizeof(double) * gk3.size(), cudaMemcpyHostToDevice, s));
   PT_CK(cudaStreamSynchronize(s));
-  PT_CK(cudaMemcpyAsync(sys->tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
-  PT_CK(cudaMemcpyAsync(sys->tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice, s));
-  if (sys->mixed) {
-    std::vector<float> kf(kt.size());
-    for (size_t t = 0; t < kt.size(); ++t) kf[t] = (float)kt[t];
-    PT_CK(cudaMemcpyAsync(sys->khat32, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice, s));
-    PT_CK(cudaStreamSynchronize(s));
-  } else {
-    PT_CK(cudaMemcpyAsync(sys->khat64, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice, s));
-  }
+  // twiddles, and the screened kernel on the Fock grid (scaled by -alpha / N_f)
+  PT_CK(upload_fft_tables(p, sys->gf, sys->mixed, sys->tw64, sys->tw32, sys->khat64, sys->khat32, s));
   if (p->n_atoms > 0)
     PT_CK(cudaMemcpyAsync(sys->d_atoms, sys->atoms.data(), sizeof(double) * 3 * p->n_atoms, cudaMemcpyHostToDevice, s));
   if (pt::sphere_fast_supported(sys->g)) {
@@ -1497,7 +1490,8 @@ pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, v
                    std::to_string(kStaticScratchBytes) + " bytes. Use pt_exchange with a workspace.";
     return PT_ERR_OOM;
   }
-  const int tpl = (int)std::min<size_t>((size_t)nb, (kStaticScratchBytes - fixed) / per_tile);
+  int tpl = (int)std::min<size_t>((size_t)nb, (kStaticScratchBytes - fixed) / per_tile);
+  if (p->pair_tiles_per_launch > 0) tpl = std::min(tpl, p->pair_tiles_per_launch);
   void* base = nullptr;
   st = static_scratch_address(&base);
   if (st != PT_OK) return st;

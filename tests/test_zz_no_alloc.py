@@ -5,8 +5,10 @@ all device memory, or code that must not allocate after start-up) use
 pt_exchange_static: its scratch is a static device array inside the library.
 Here it is called through the C ABI twice in a row on the orbitals of a
 system built by pt_init_system, and each result is compared with
-pt_exchange of that system, to the tolerances of the parity tests. A system
-too large for the array must be refused with PT_ERR_OOM. (The test itself
+pt_exchange of that system and with the FP64 oracle's V_X Psi (Eq. 3) for the
+same orbitals, to the tolerances of the parity tests; a cap on the pair tiles
+per launch (pair_tiles_per_launch) must give the same result. A system too
+large for the array must be refused with PT_ERR_OOM. (The test itself
 allocates its input and output buffers with torch; only the entry point
 under test must not allocate.)
 """
@@ -16,6 +18,8 @@ import numpy as np
 import pytest
 
 import synthetic as syn
+from oracle import discretization as dz
+from oracle import exchange as ex
 
 pytestmark = pytest.mark.gpu
 
@@ -44,11 +48,17 @@ def test_static_exchange_matches_workspace_exchange(pkg, precision, tol):
     s = pkg.System(w, C0)
     ref = s.exchange().cpu().numpy()
     psi = s.orbitals_device()
+    grid = dz.Grid(w["n"], w["cell"], w["ecut"])
+    Psi = psi.cpu().numpy().T
+    oracle_w = ex.apply_vx(grid, ex.screened_kernel(grid, w["omega"]), w["alpha"], Psi, Psi).T
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):
+    for tpl in (0, 0, 3):
+        p_call = pkg.make_params(dict(w, pair_tiles_per_launch=tpl))
         out = torch.full(psi.shape, float("nan"), dtype=torch.complex128, device=psi.device)
-        pkg.pt_exchange_static(params, psi.data_ptr(), out.data_ptr(), stream)
-        assert rel(out.cpu().numpy(), ref) < tol
+        pkg.pt_exchange_static(p_call, psi.data_ptr(), out.data_ptr(), stream)
+        got = out.cpu().numpy()
+        assert rel(got, ref) < tol
+        assert rel(got, oracle_w) < tol
     s.close()
 
 
