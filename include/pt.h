@@ -46,7 +46,7 @@ typedef enum pt_status {
   PT_ERR_CUDA = 3,           /* a CUDA runtime call failed */
   PT_ERR_NOT_CONVERGED = 4,  /* SCF loop reached scf_max (state still advanced) */
   PT_ERR_NOT_PD = 5,         /* Cholesky met a non-positive pivot */
-  PT_ERR_TIMEOUT = 6         /* reserved: the kernels have no device-side waits */
+  PT_ERR_TIMEOUT = 6         /* a bounded wait inside a tensor-core kernel expired */
 } pt_status;
 
 enum { PT_FP64 = 0, PT_MIXED = 1 };                       /* precision */
@@ -95,6 +95,20 @@ typedef struct pt_params {
    * products, as the paper's exchange on its wavefunction grid (Sec. 4); the orbitals are
    * transformed onto it for every exchange. pt_exchange_static does not support it. */
   int n_fock[3];
+  /* Mixed precision only (iterative refinement of Alg. 1's fixed point): when scf_tol is
+   * below this value (> 0), the residual R_n of the half step and every SCF iteration
+   * after the density change has fallen below it evaluate H Psi (local potential,
+   * ACE, PT projection) and R_f in FP64, so the iteration converges past the FP32
+   * rounding floor (about 1e-8 in the density change). 0 = FP32 throughout. The
+   * exchange of exact mode (PT_FOCK_EXACT) keeps its FP32 pair FFTs. */
+  double scf_fp64_below;
+  /* PT_FOCK_ACE only: after the SCF of a step has converged with ACE built from Psi_n,
+   * rebuild ACE from the converged Psi_f (its exchange W = V_X Psi_f, M = Psi_f^H W,
+   * -M = L L^H, xi = W L^{-H}) and run the SCF again (Anderson history restarted), this
+   * many times per step. Each rebuild raises the order in dt of the difference to exact
+   * exchange every iteration by one, at the cost of one exchange per rebuild. 0: ACE once
+   * per step. */
+  int ace_outer;
 } pt_params;
 
 typedef struct pt_system pt_system;
@@ -210,6 +224,26 @@ pt_status pt_set_state(pt_system* sys, const double* psi_host, const double* w_h
  * systems); differences of two readings count the launches in between. */
 pt_status pt_launch_count(uint64_t* count);
 
+/* The complex products of ACE and of the PT residual as the mixed-precision path
+ * computes them on the tensor cores: C = alpha op(A) op(B) + beta C, the
+ * contractions M = Psi^H W, xi = W L^{-H}, xi^H X and -xi (xi^H X) of ACE (cited
+ * in Sec. 1) and S = Psi^H (H Psi), H Psi - Psi S of Alg. 3. A and B are
+ * complex64 (interleaved re, im), C is complex128, all column-major on the device:
+ * element (i, k) of op(A) is A[i + k lda] for op_a = 0 and conj(A[k + i lda]) for
+ * op_a = 1; likewise op(B) with ldb. op(A) is M x K, op(B) K x N, C M x N (ldc).
+ * upper_b = 1 promises that op(B) is upper triangular (op(B)(k, j) = 0 for k > j),
+ * which lets each output tile stop its reduction at its last column. Arithmetic: 3xTF32 (each operand split into two TF32 parts,
+ * three products) with FP32 accumulation. d_ws: device scratch of ws_bytes >= 256
+ * (256-byte aligned): its first 256 bytes hold a status word, the rest takes the
+ * split-K partials of long reductions (M N complex128 per split; with no room the
+ * reduction is not split). Enqueued on `stream`, which is synchronised before the
+ * call returns (A and B may be NULL when K = 0: then C = beta C). Errors:
+ * PT_ERR_INVALID for bad sizes or pointers, PT_ERR_TIMEOUT if
+ * a bounded wait inside the kernel expired, PT_ERR_CUDA for a failed launch. */
+pt_status pt_complex_product(int op_a, int op_b, int M, int N, int K, const double* alpha2, const void* d_A,
+                             int64_t lda, const void* d_B, int64_t ldb, const double* beta2, void* d_C, int64_t ldc,
+                             int upper_b, void* d_ws, size_t ws_bytes, void* stream);
+
 /* V_X Psi without any device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc (a plug-in whose
  * host application owns all device memory through its own allocator, or code
@@ -229,6 +263,45 @@ pt_status pt_launch_count(uint64_t* count);
  * array and overwrites its contents (the accumulators are cleared by each
  * call): calls that overlap on the GPU, from any stream or thread, race. */
 pt_status pt_exchange_static(const pt_params* p, const void* d_psi, void* d_w, void* stream);
+
+/* Batches: several systems stepped together (no counterpart in the paper, which batches
+ * the pair FFTs of one system into library calls, Sec. 3.2). The systems must share the
+ * grid, Fock grid, precision, cell, cutoff and screened kernel (omega, alpha != 0); their
+ * orbital counts, kicks, lasers and start states may differ. The pair tiles of all
+ * systems go into shared launch groups: round r of every system's tile tournament
+ * (Eq. 3, the pair loop of Alg. 2) forms one merged round, split into launch groups of
+ * at most tiles_per_launch tiles (0: whole rounds, up to a 16 GB pair intermediate), with
+ * pair_tile orbitals per tile edge (0: min(4, largest n_orb)). The merged pair-kernel
+ * sequence is captured into a CUDA graph after its first run and replayed. With the same
+ * pair_tile as a system's own (pt_params.pair_tile), batched results are bitwise those
+ * of the system stepped alone.
+ * pt_batch_workspace_size: device bytes pt_batch_create needs for these systems.
+ * pt_batch_create: systems (nsys >= 1, distinct, created by pt_init_system and kept alive
+ *   until pt_batch_destroy), a device workspace (256-byte aligned, caller-owned, not
+ *   shared with the systems' workspaces) and a created stream (not the NULL stream: the
+ *   graph is captured on it) for the merged pair kernels; the systems keep their own
+ *   streams, ordered against the batch stream by events. Errors: PT_ERR_INVALID
+ *   (incompatible systems, bad arguments), PT_ERR_OOM (workspace too small).
+ * pt_batch_exchange: W = V_X Psi of every system's current orbitals into d_w[i]
+ *   (npw x n_orb complex128, device), synchronising the systems' streams.
+ * pt_batch_step: one PT-CN step (Eq. 5, Alg. 1) of every system, out_host[i] (may be
+ *   NULL) receiving system i's step information. The SCF iterations of all systems are
+ *   interleaved on their streams; the exchange of the new orbitals is the merged launch
+ *   sequence. Returns PT_ERR_NOT_CONVERGED if any system reached scf_max (all steps are
+ *   still taken), another error naming the system otherwise.
+ * pt_batch_set_timing / pt_batch_get_timing: CUDA-event time of the merged pair kernels
+ *   on the batch stream, as pt_set_timing / pt_get_timing.
+ * Errors of batch calls are reported through pt_last_error(NULL) on the calling thread. */
+typedef struct pt_batch pt_batch;
+pt_status pt_batch_workspace_size(pt_system* const* systems, int nsys, int pair_tile, int tiles_per_launch,
+                                  size_t* bytes);
+pt_status pt_batch_create(pt_system* const* systems, int nsys, int pair_tile, int tiles_per_launch, void* d_ws,
+                          size_t ws_bytes, void* stream, pt_batch** out);
+pt_status pt_batch_exchange(pt_batch* b, void* const* d_w);
+pt_status pt_batch_step(pt_batch* b, pt_step_info* out_host);
+pt_status pt_batch_set_timing(pt_batch* b, int enable);
+pt_status pt_batch_get_timing(pt_batch* b, double* pair_ms, int64_t* pairs, int64_t* launch_groups, int reset);
+pt_status pt_batch_destroy(pt_batch* b);
 
 /* Release the handle (the workspace stays owned by the caller). */
 pt_status pt_destroy(pt_system* s);

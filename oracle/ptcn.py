@@ -32,7 +32,12 @@ Readings (the paper is silent on these details):
 * Fock modes: "exact" re-evaluates V_X[Psi_f] Psi_f every iteration (the paper's
   GPU path, 24 exchange evaluations per step, Sec. 6); "ace" builds the ACE
   operator once from Psi_n and keeps it through the loop. Rebuilding ACE from
-  Psi_f every iteration equals "exact" for H_f Psi_f.
+  Psi_f every iteration equals "exact" for H_f Psi_f. With ``ace_outer`` = k > 0
+  the "ace" step, once its SCF has converged, rebuilds ACE from the converged
+  Psi_f and runs the SCF again (restarted Anderson history), k times: the
+  operator then tracks Psi_{n+1} instead of Psi_n. Building ACE once per step
+  perturbs H_f by O(dt), so one step differs from "exact" by O(dt^2) (pinned:
+  tests/test_oracle_ptcn.py).
 * The exchange data of Psi_{n+1} (W = V_X Psi_{n+1}, and the ACE operator) are
   produced at the end of a step, where they also give the energy E_{n+1}, and
   the next step reuses them for R_n.
@@ -108,6 +113,7 @@ class Params:
     laser_duration: float = 1240.4    # pulse length T (a.u.): 30 fs
     laser_dir: tuple = (1.0, 0.0, 0.0)
     fock_grid: tuple = None           # grid of the pair FFTs; None: the grid n (alias-free)
+    ace_outer: int = 0                # "ace" mode: ACE rebuilds from the converged Psi_f per step
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -245,37 +251,47 @@ class Model:
         Psi_f = Psi_half.copy()
         rho_f = self.density(Psi_f)
 
-        mix = Anderson(p.anderson_dim, p.anderson_beta)
         fixed = int(p.scf_fixed_iters)
         n_iter = fixed if fixed > 0 else int(p.scf_max)
-        converged = False
         resid = np.inf
         drho = np.inf
-        it = 0
-        for it in range(1, n_iter + 1):
-            # update the potential and H_f
-            vloc = self.local.local_potential(rho_f)
-            HPf = self.local.apply_local(vloc, Psi_f, kin_f)
-            if p.alpha != 0.0:
-                if p.fock_mode == "exact":
-                    HPf = HPf + self.vx(Psi_f, Psi_f)
-                else:
-                    HPf = HPf + ex.apply_ace(st.xi, Psi_f)
-            # fixed-point residual R_f (computed as in Alg. 3)
-            S_f = Psi_f.conj().T @ HPf
-            R_f = Psi_f + 0.5j * dt * (HPf - Psi_f @ S_f) - Psi_half
-            resid = float(np.linalg.norm(R_f))
-            # Anderson mixing
-            Psi_f = mix.update(Psi_f, -R_f)
-            # new density, convergence test
-            rho_new = self.density(Psi_f)
-            drho = float(g.dV * np.sum(np.abs(rho_new - rho_f)) / n_el)
-            rho_f = rho_new
-            if fixed == 0 and drho < p.scf_tol:
+        total = 0
+        xi = st.xi
+        outer_left = int(p.ace_outer) if (p.fock_mode == "ace" and p.alpha != 0.0) else 0
+        while True:
+            mix = Anderson(p.anderson_dim, p.anderson_beta)
+            converged = False
+            for _ in range(n_iter):
+                total += 1
+                # update the potential and H_f
+                vloc = self.local.local_potential(rho_f)
+                HPf = self.local.apply_local(vloc, Psi_f, kin_f)
+                if p.alpha != 0.0:
+                    if p.fock_mode == "exact":
+                        HPf = HPf + self.vx(Psi_f, Psi_f)
+                    else:
+                        HPf = HPf + ex.apply_ace(xi, Psi_f)
+                # fixed-point residual R_f (computed as in Alg. 3)
+                S_f = Psi_f.conj().T @ HPf
+                R_f = Psi_f + 0.5j * dt * (HPf - Psi_f @ S_f) - Psi_half
+                resid = float(np.linalg.norm(R_f))
+                # Anderson mixing
+                Psi_f = mix.update(Psi_f, -R_f)
+                # new density, convergence test
+                rho_new = self.density(Psi_f)
+                drho = float(g.dV * np.sum(np.abs(rho_new - rho_f)) / n_el)
+                rho_f = rho_new
+                if fixed == 0 and drho < p.scf_tol:
+                    converged = True
+                    break
+            if fixed > 0:
                 converged = True
+            if outer_left == 0:
                 break
-        if fixed > 0:
-            converged = True
+            # outer ACE rebuild: the operator of the converged Psi_f, then the SCF again
+            outer_left -= 1
+            _, _, _, xi = ex.build_ace(self.fgrid, self.khat, p.alpha, Psi_f)
+        it = total
 
         # orthonormalise, then the exchange data and observables of Psi_{n+1}
         Psi_next = orthonormalize(Psi_f)

@@ -55,6 +55,8 @@ class PtParams(C.Structure):
         ("laser_duration", C.c_double),
         ("laser_dir", C.c_double * 3),
         ("n_fock", C.c_int * 3),
+        ("scf_fp64_below", C.c_double),
+        ("ace_outer", C.c_int),
     ]
 
 
@@ -114,6 +116,17 @@ def load() -> C.CDLL:
         "pt_get_timing": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int]),
         "pt_launch_count": (C.c_int, [C.POINTER(C.c_uint64)]),
         "pt_exchange_static": (C.c_int, [P, vp, vp, vp]),
+        "pt_complex_product": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp,
+                                         C.c_int64, vp, C.c_int64, C.POINTER(C.c_double), vp, C.c_int64, C.c_int,
+                                         vp, C.c_size_t, vp]),
+        "pt_batch_workspace_size": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+        "pt_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.c_int, vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "pt_batch_exchange": (C.c_int, [vp, C.POINTER(vp)]),
+        "pt_batch_step": (C.c_int, [vp, C.POINTER(PtStepInfo)]),
+        "pt_batch_set_timing": (C.c_int, [vp, C.c_int]),
+        "pt_batch_get_timing": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                          C.c_int]),
+        "pt_batch_destroy": (C.c_int, [vp]),
         "pt_destroy": (C.c_int, [vp]),
         "pt_last_error": (C.c_char_p, [vp]),
     }
@@ -172,6 +185,8 @@ def make_params(d: dict) -> PtParams:
     ld = d.get("laser_dir", (1.0, 0.0, 0.0))
     for k in range(3):
         p.laser_dir[k] = float(ld[k])
+    p.scf_fp64_below = float(d.get("scf_fp64_below", 0.0))
+    p.ace_outer = int(d.get("ace_outer", 0))
     nf = d.get("fock_grid") or (0, 0, 0)
     for k in range(3):
         p.n_fock[k] = int(nf[k])
@@ -303,6 +318,63 @@ def pt_get_timing(h, reset: bool = False) -> tuple[float, int, int]:
 def pt_exchange_static(params: PtParams, d_psi: int, d_w: int, stream: int = 0) -> None:
     """V_X Psi with no device allocation (scratch in a static 64 MiB device array)."""
     _check(load().pt_exchange_static(C.byref(params), C.c_void_p(d_psi), C.c_void_p(d_w), C.c_void_p(stream)))
+
+
+def pt_complex_product(op_a: int, op_b: int, M: int, N: int, K: int, alpha: complex, d_A: int, lda: int, d_B: int,
+                       ldb: int, beta: complex, d_C: int, ldc: int, upper_b: bool, d_ws: int, ws_bytes: int,
+                       stream: int = 0) -> None:
+    """C = alpha op(A) op(B) + beta C (complex64 A, B; complex128 C) on the tensor cores."""
+    a = (C.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    b = (C.c_double * 2)(complex(beta).real, complex(beta).imag)
+    _check(load().pt_complex_product(int(op_a), int(op_b), int(M), int(N), int(K), a, C.c_void_p(d_A), int(lda),
+                                     C.c_void_p(d_B), int(ldb), b, C.c_void_p(d_C), int(ldc), int(bool(upper_b)),
+                                     C.c_void_p(d_ws), int(ws_bytes), C.c_void_p(stream)))
+
+
+def _handles(handles):
+    arr = (C.c_void_p * len(handles))()
+    for k, h in enumerate(handles):
+        arr[k] = h.value if isinstance(h, C.c_void_p) else h
+    return arr
+
+
+def pt_batch_workspace_size(handles, pair_tile: int = 0, tiles_per_launch: int = 0) -> int:
+    n = C.c_size_t(0)
+    _check(load().pt_batch_workspace_size(_handles(handles), len(handles), int(pair_tile), int(tiles_per_launch),
+                                          C.byref(n)))
+    return n.value
+
+
+def pt_batch_create(handles, pair_tile: int, tiles_per_launch: int, d_ws: int, ws_bytes: int, stream: int):
+    b = C.c_void_p()
+    _check(load().pt_batch_create(_handles(handles), len(handles), int(pair_tile), int(tiles_per_launch),
+                                  C.c_void_p(d_ws), int(ws_bytes), C.c_void_p(stream), C.byref(b)))
+    return b
+
+
+def pt_batch_exchange(b, d_w_ptrs) -> None:
+    _check(load().pt_batch_exchange(b, _handles(d_w_ptrs)))
+
+
+def pt_batch_step(b, nsys: int):
+    """One PT-CN step of every system; returns (status, [info dict per system])."""
+    infos = (PtStepInfo * nsys)()
+    st = _check(load().pt_batch_step(b, infos), allow=(PT_ERR_NOT_CONVERGED,))
+    return st, [infos[k].as_dict() for k in range(nsys)]
+
+
+def pt_batch_set_timing(b, enable: bool) -> None:
+    _check(load().pt_batch_set_timing(b, int(bool(enable))))
+
+
+def pt_batch_get_timing(b, reset: bool = False):
+    ms, pairs, groups = C.c_double(0), C.c_int64(0), C.c_int64(0)
+    _check(load().pt_batch_get_timing(b, C.byref(ms), C.byref(pairs), C.byref(groups), int(bool(reset))))
+    return ms.value, pairs.value, groups.value
+
+
+def pt_batch_destroy(b) -> None:
+    load().pt_batch_destroy(b)
 
 
 def pt_launch_count() -> int:

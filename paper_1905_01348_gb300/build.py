@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libptfock.so")
-SOURCES = ["fft3d.cu", "fft_sphere.cu", "fock.cu", "fock_fast.cu", "linalg.cu", "kernels.cu", "api.cu"]
+SOURCES = ["fft3d.cu", "fft_sphere.cu", "fock.cu", "fock_fast.cu", "linalg.cu", "gemm_tc.cu", "kernels.cu", "setup.cu", "engine.cu", "batch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -38,8 +38,7 @@ static const cplx<T>* twp(const DevTwiddles& tw, int L) {
 
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_fock_f1(const cplx<T>* __restrict__ psi_r, const cplx<T>* __restrict__ x_r,
-                          const PairTile* __restrict__ tiles, int tile0, cplx<T>* __restrict__ X, int n0, int n1,
+__global__ void k_fock_f1(const PairTile* __restrict__ tiles, int tile0, cplx<T>* __restrict__ X, int n0, int n1,
                           int n2, int rr, const cplx<T>* __restrict__ tw_g) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -55,10 +54,9 @@ __global__ void k_fock_f1(const cplx<T>* __restrict__ psi_r, const cplx<T>* __re
   const int nb1 = n1 / rr;
   const int i0 = blockIdx.x / nb1;
   const int i1s = (blockIdx.x - i0 * nb1) * rr;
-  const long N = (long)n0 * n1 * n2;
   const long roff = ((long)i0 * n1 + i1s) * n2;
   for (int o = 0; o < tl.n_orb; ++o) {
-    const C* src = (tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N + roff;
+    const C* src = (const C*)tl.in[o] + roff;
     for (int e = tid; e < rowlen; e += nthr) orb[o * rowlen + e] = src[e];
   }
   __syncthreads();
@@ -111,9 +109,8 @@ __global__ void __launch_bounds__(768, 1) k_fock_f2(cplx<T>* __restrict__ X, con
 }
 
 template <typename T>
-__global__ void k_fock_f3(const cplx<T>* __restrict__ psi_r, const cplx<T>* __restrict__ x_r,
-                          cplx<T>* __restrict__ w_occ, cplx<T>* __restrict__ w_x, const PairTile* __restrict__ tiles,
-                          int tile0, const cplx<T>* __restrict__ X, int n0, int n1, int n2, int rr, int sym,
+__global__ void k_fock_f3(const PairTile* __restrict__ tiles, int tile0, const cplx<T>* __restrict__ X, int n0, int n1,
+                          int n2, int rr, int sym,
                           const cplx<T>* __restrict__ tw_g) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -129,7 +126,6 @@ __global__ void k_fock_f3(const cplx<T>* __restrict__ psi_r, const cplx<T>* __re
   const int nb1 = n1 / rr;
   const int i0 = blockIdx.x / nb1;
   const int i1s = (blockIdx.x - i0 * nb1) * rr;
-  const long N = (long)n0 * n1 * n2;
   const long roff = ((long)i0 * n1 + i1s) * n2;
   const int np = tl.n_pairs;
   const long slot0 = (long)blockIdx.y * kTileMax * kTileMax;
@@ -141,7 +137,7 @@ __global__ void k_fock_f3(const cplx<T>* __restrict__ psi_r, const cplx<T>* __re
     work[(p * rr + r) * n2 + i2] = X[(((slot0 + p) * n2 + i2) * n0 + i0) * n1 + i1s + r];
   }
   for (int o = 0; o < tl.n_orb; ++o) {
-    const C* src = (tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N + roff;
+    const C* src = (const C*)tl.in[o] + roff;
     for (int e = tid; e < rowlen; e += nthr) orb[o * rowlen + e] = src[e];
   }
   __syncthreads();
@@ -149,7 +145,7 @@ __global__ void k_fock_f3(const cplx<T>* __restrict__ psi_r, const cplx<T>* __re
   // each output orbital: fixed-order sum over the tile's pairs, one RMW of its row
   for (int o = 0; o < tl.n_orb; ++o) {
     if (!tl.is_out[o]) continue;
-    C* dst = (tl.src[o] == 0 ? w_occ : w_x) + (long)tl.orb[o] * N + roff;
+    C* dst = (C*)tl.out[o] + roff;
     for (int e = tid; e < rowlen; e += nthr) {
       C acc = mk((T)0, (T)0);
       for (int p = 0; p < np; ++p) {
@@ -176,12 +172,11 @@ static int round_threads(int t) {
 }
 
 template <typename T>
-cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
-                       Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s) {
+cudaError_t fock_pairs(const FockPlan& plan, int sym, Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw,
+                       cudaStream_t s) {
   using C = cplx<T>;
   if constexpr (sizeof(T) == 4) {
-    if (fock_fast_supported(g))
-      return fock_pairs_fast(psi_r, x_r, w_occ, w_x, plan, g, khat_t, scratch, twp<float>(tw, g.n0), s);
+    if (fock_fast_supported(g)) return fock_pairs_fast(plan, g, khat_t, scratch, twp<float>(tw, g.n0), s);
   }
   const bool fp64 = sizeof(T) == 8;
   const int rr = rows_per_block(g.n1, fp64);
@@ -211,20 +206,33 @@ cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_
   for (int l = 0; l < plan.n_launch; ++l) {
     const int t0 = plan.launch_first[l], nt = plan.launch_count[l];
     dim3 g13((unsigned)(g.n0 * (g.n1 / rr)), (unsigned)nt);
-    k_fock_f1<T><<<g13, thr13, smem13, s>>>((const C*)psi_r, (const C*)x_r, plan.d_tiles, t0, X, g.n0, g.n1, g.n2, rr,
-                                           tw2); launched();
+    k_fock_f1<T><<<g13, thr13, smem13, s>>>(plan.d_tiles, t0, X, g.n0, g.n1, g.n2, rr, tw2); launched();
     dim3 g2((unsigned)g.n2, (unsigned)(nt * kTileMax * kTileMax));
     k_fock_f2<T><<<g2, thr2, smem2, s>>>(X, plan.d_tiles, t0, g.n0, g.n1, g.n2, khat_t, tw0, tw1); launched();
-    k_fock_f3<T><<<g13, thr13, smem13, s>>>((const C*)psi_r, (const C*)x_r, (C*)w_occ, (C*)w_x, plan.d_tiles, t0, X,
-                                           g.n0, g.n1, g.n2, rr, sym, tw2); launched();
+    k_fock_f3<T><<<g13, thr13, smem13, s>>>(plan.d_tiles, t0, X, g.n0, g.n1, g.n2, rr, sym, tw2); launched();
   }
   return cudaGetLastError();
 }
 
-template cudaError_t fock_pairs<float>(const void*, const void*, void*, void*, const FockPlan&, int, Grid3,
-                                       const float*, void*, const DevTwiddles&, cudaStream_t);
-template cudaError_t fock_pairs<double>(const void*, const void*, void*, void*, const FockPlan&, int, Grid3,
-                                        const double*, void*, const DevTwiddles&, cudaStream_t);
+template cudaError_t fock_pairs<float>(const FockPlan&, int, Grid3, const float*, void*, const DevTwiddles&,
+                                       cudaStream_t);
+template cudaError_t fock_pairs<double>(const FockPlan&, int, Grid3, const double*, void*, const DevTwiddles&,
+                                        cudaStream_t);
+
+void fock_bind_tiles(PairTile* tiles, int n, const void* psi_r, const void* x_r, void* w_occ, void* w_x, long N,
+                     size_t cs) {
+  for (int t = 0; t < n; ++t) {
+    PairTile& tl = tiles[t];
+    for (int o = 0; o < 2 * kTileMax; ++o) {
+      tl.in[o] = nullptr;
+      tl.out[o] = nullptr;
+      if (o >= tl.n_orb) continue;
+      const size_t off = (size_t)tl.orb[o] * (size_t)N * cs;
+      tl.in[o] = (const unsigned char*)(tl.src[o] == 0 ? psi_r : x_r) + off;
+      if (tl.is_out[o]) tl.out[o] = (unsigned char*)(tl.src[o] == 0 ? w_occ : w_x) + off;
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Tile schedule. Symmetric: blocks of `tile` orbitals; rounds of a

@@ -52,10 +52,10 @@ template <int L> __device__ __forceinline__ bool dead_slab(int i2, int reach) { 
 // pair 4a + b = (a, 4 + b).
 __device__ __forceinline__ bool full_tile(const PairTile& tl) { return tl.n_orb == 2 * TT && tl.n_pairs == NPAIR; }
 
-__device__ __forceinline__ const float2* orb_ptr(const PairTile& tl, int o, const float2* psi_r, const float2* x_r,
-                                                 long N) {
-  return (tl.src[o] == 0 ? psi_r : x_r) + (long)tl.orb[o] * N;
+__device__ __forceinline__ const float2* orb_ptr(const PairTile& tl, int o) {
+  return static_cast<const float2*>(tl.in[o]);
 }
+__device__ __forceinline__ float2* acc_ptr(const PairTile& tl, int o) { return static_cast<float2*>(tl.out[o]); }
 
 }  // namespace
 
@@ -64,9 +64,7 @@ __device__ __forceinline__ const float2* orb_ptr(const PairTile& tl, int o, cons
 // all their loads issued first), forward FFT along axis 2, store the live
 // slabs of X[slot][i2][i0][i1].
 template <int L>
-__global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __restrict__ psi_r,
-                                                          const float2* __restrict__ x_r,
-                                                          const PairTile* __restrict__ tiles, int tile0,
+__global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const PairTile* __restrict__ tiles, int tile0,
                                                           float2* __restrict__ X, const float2* __restrict__ tw_g,
                                                           int reach) {
   using A = RowsT<L>;
@@ -92,7 +90,7 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
     for (int e = tid; e < ROW; e += NT) {
       float2 v[2 * TT];
 #pragma unroll
-      for (int o = 0; o < 2 * TT; ++o) v[o] = __ldg(orb_ptr(tl, o, psi_r, x_r, N) + roff + e);
+      for (int o = 0; o < 2 * TT; ++o) v[o] = __ldg(orb_ptr(tl, o) + roff + e);
       const int row = e / L, col = e % L;
 #pragma unroll
       for (int a = 0; a < TT; ++a)
@@ -109,8 +107,8 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const float2* __res
         const int idx = base + u * NT;
         if (idx < np * ROW) {
           const int p = idx / ROW, e = idx % ROW;
-          a[u] = __ldg(orb_ptr(tl, tl.pi[p], psi_r, x_r, N) + roff + e);
-          b[u] = __ldg(orb_ptr(tl, tl.pj[p], psi_r, x_r, N) + roff + e);
+          a[u] = __ldg(orb_ptr(tl, tl.pi[p]) + roff + e);
+          b[u] = __ldg(orb_ptr(tl, tl.pj[p]) + roff + e);
         }
       }
 #pragma unroll
@@ -202,10 +200,8 @@ __global__ void __launch_bounds__(Cfg2<L>::NT, Cfg2<L>::MINB) k_fast_f2(float2* 
 // Three resident blocks per SM (rather than F1's four) leave F3 the registers to keep the
 // orbital and W loads of its accumulation in flight together (9% faster at 96^3).
 template <int L>
-__global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const float2* __restrict__ psi_r,
-                                                          const float2* __restrict__ x_r, float2* __restrict__ w_occ,
-                                                          float2* __restrict__ w_x, const PairTile* __restrict__ tiles,
-                                                          int tile0, const float2* __restrict__ X,
+__global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const PairTile* __restrict__ tiles, int tile0,
+                                                          const float2* __restrict__ X,
                                                           const float2* __restrict__ tw_g, int reach) {
   using A = RowsT<L>;
   constexpr int NT = Cfg<L>::NT13;
@@ -247,8 +243,8 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const float2* __res
       float2* dst[2 * TT];
 #pragma unroll
       for (int o = 0; o < 2 * TT; ++o) {
-        v[o] = __ldg(orb_ptr(tl, o, psi_r, x_r, N) + roff + e);
-        dst[o] = (tl.src[o] == 0 ? w_occ : w_x) + (long)tl.orb[o] * N + roff + e;
+        v[o] = __ldg(orb_ptr(tl, o) + roff + e);
+        dst[o] = tl.is_out[o] ? acc_ptr(tl, o) + roff + e : nullptr;
         if (tl.is_out[o]) w[o] = *dst[o];
       }
 #pragma unroll
@@ -273,13 +269,13 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const float2* __res
   for (int o = 0; o < tl.n_orb; ++o) {
     const int n = tl.out_n[o];
     if (!tl.is_out[o] || n == 0) continue;
-    float2* dst = (tl.src[o] == 0 ? w_occ : w_x) + (long)tl.orb[o] * N + roff;
+    float2* dst = acc_ptr(tl, o) + roff;
     for (int e = tid; e < ROW; e += NT) {
       const int r = e / L, i2 = e % L;
       float2 acc = make_float2(0.f, 0.f);
       for (int c = 0; c < n; ++c) {
         const float2 v = work[A::at(tl.out_pair[o][c] * RR + r, i2)];
-        const float2 a = __ldg(orb_ptr(tl, tl.out_other[o][c], psi_r, x_r, N) + roff + e);
+        const float2 a = __ldg(orb_ptr(tl, tl.out_other[o][c]) + roff + e);
         acc = cadd(acc, tl.out_conj[o][c] ? cmul_conj(a, v) : cmul(a, v));
       }
       dst[e] = cadd(dst[e], acc);
@@ -288,8 +284,8 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const float2* __res
 }
 
 template <int L>
-static cudaError_t launch_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan,
-                               const float* khat_t, void* scratch, const float2* tw, cudaStream_t s) {
+static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* scratch, const float2* tw,
+                               cudaStream_t s) {
   static std::atomic<unsigned long long> attr_done{0};
   if (const unsigned long long bit = device_bit_todo(attr_done)) {
     cudaError_t e = cudaFuncSetAttribute(k_fast_f1<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
@@ -306,12 +302,10 @@ static cudaError_t launch_fast(const void* psi_r, const void* x_r, void* w_occ, 
   for (int l = 0; l < plan.n_launch; ++l) {
     const int t0 = plan.launch_first[l], nt = plan.launch_count[l];
     dim3 g13((unsigned)(L * (L / RR)), (unsigned)nt);
-    k_fast_f1<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>((const float2*)psi_r, (const float2*)x_r, plan.d_tiles, t0, X,
-                                                         tw, reach);
+    k_fast_f1<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     dim3 g2((unsigned)n_live, (unsigned)(nt * NPAIR));
     k_fast_f2<L><<<g2, Cfg2<L>::NT, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
-    k_fast_f3<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>((const float2*)psi_r, (const float2*)x_r, (float2*)w_occ,
-                                                         (float2*)w_x, plan.d_tiles, t0, X, tw, reach);
+    k_fast_f3<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     launched(3);
   }
   return cudaGetLastError();
@@ -321,13 +315,13 @@ bool fock_fast_supported(Grid3 g) {
   return g.n0 == g.n1 && g.n1 == g.n2 && (g.n0 == 32 || g.n0 == 48 || g.n0 == 64 || g.n0 == 96);
 }
 
-cudaError_t fock_pairs_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, Grid3 g,
-                            const float* khat_t, void* scratch, const float2* tw_L, cudaStream_t s) {
+cudaError_t fock_pairs_fast(const FockPlan& plan, Grid3 g, const float* khat_t, void* scratch, const float2* tw_L,
+                            cudaStream_t s) {
   switch (g.n0) {
-    case 32: return launch_fast<32>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
-    case 48: return launch_fast<48>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
-    case 64: return launch_fast<64>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
-    case 96: return launch_fast<96>(psi_r, x_r, w_occ, w_x, plan, khat_t, scratch, tw_L, s);
+    case 32: return launch_fast<32>(plan, khat_t, scratch, tw_L, s);
+    case 48: return launch_fast<48>(plan, khat_t, scratch, tw_L, s);
+    case 64: return launch_fast<64>(plan, khat_t, scratch, tw_L, s);
+    case 96: return launch_fast<96>(plan, khat_t, scratch, tw_L, s);
     default: return cudaErrorInvalidValue;
   }
 }

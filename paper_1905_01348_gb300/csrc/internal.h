@@ -85,6 +85,11 @@ cudaError_t sphere_from_real(const double2* vol, const double* mul, double2* wor
 // ---- Fock exchange pair pipeline (fock.cu) ----------------------------------
 constexpr int kTileMax = 4;
 struct PairTile {
+  // device addresses of the real-space rows of slot o (exchange precision) and of its
+  // accumulator (when is_out[o]); set by fock_bind_tiles, so the tiles of one launch
+  // group may belong to different systems
+  const void* in[2 * kTileMax];
+  void* out[2 * kTileMax];
   int n_orb;
   int n_pairs;
   int orb[2 * kTileMax];
@@ -117,13 +122,19 @@ struct FockPlan {
   int g2_reach;
 };
 
+// The pair kernels of `plan` (tiles bound to their orbitals and accumulators).
 template <typename T>
-cudaError_t fock_pairs(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, int sym,
-                       Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw, cudaStream_t s);
+cudaError_t fock_pairs(const FockPlan& plan, int sym, Grid3 g, const T* khat_t, void* scratch, const DevTwiddles& tw,
+                       cudaStream_t s);
 // FP32 cubic fast path (fock_fast.cu): n0 == n1 == n2 in {32, 48, 64, 96}.
 bool fock_fast_supported(Grid3 g);
-cudaError_t fock_pairs_fast(const void* psi_r, const void* x_r, void* w_occ, void* w_x, const FockPlan& plan, Grid3 g,
-                            const float* khat_t, void* scratch, const float2* tw_L, cudaStream_t s);
+cudaError_t fock_pairs_fast(const FockPlan& plan, Grid3 g, const float* khat_t, void* scratch, const float2* tw_L,
+                            cudaStream_t s);
+// Sets in[] / out[] of host tiles from their orbital slots: slot o reads
+// (src 0 ? psi_r : x_r) + orb * N and accumulates into (src 0 ? w_occ : w_x) + orb * N,
+// N complex values of `cs` bytes per orbital.
+void fock_bind_tiles(PairTile* tiles, int n, const void* psi_r, const void* x_r, void* w_occ, void* w_x, long N,
+                     size_t cs);
 // Host tile schedules. sym: pairs i <= j of n_occ orbitals; otherwise n_occ x n_x pairs.
 int fock_build_tiles(int n_occ, int n_x, int tile, int sym, int tiles_per_launch, PairTile** tiles_out,
                      int** launch_first, int** launch_count, int* n_launch);
@@ -141,10 +152,15 @@ cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const dou
                  const double2* B, long ldb, long strideB, double2 beta, double2* C, long ldc, long strideC,
                  int batch, double2* splitk_ws, size_t splitk_ws_elems, cudaStream_t s,
                  int structure = GEMM_GENERAL);
-// The same product from complex64 copies of A and B, computed in FP32 (C stays complex128).
-cudaError_t gemm_c64(int opA, int opB, int M, int N, int K, double2 alpha, const float2* A, long lda, const float2* B,
-                     long ldb, double2 beta, double2* C, long ldc, double2* splitk_ws, size_t splitk_ws_elems,
-                     cudaStream_t s, int structure = GEMM_GENERAL);
+// The same product from complex64 copies of A and B on the tensor cores (gemm_tc.cu):
+// 3xTF32 with FP32 accumulation, C complex128; GEMM_GENERAL or GEMM_TRI_B. `d_err`
+// (device int) gets bit 0 set when a bounded wait inside the kernel expires.
+cudaError_t gemm_tc(int opA, int opB, int M, int N, int K, double2 alpha, const float2* A, long lda, const float2* B,
+                    long ldb, double2 beta, double2* C, long ldc, double2* splitk_ws, size_t splitk_ws_elems,
+                    int* d_err, cudaStream_t s, int structure = GEMM_GENERAL);
+// C = alpha sum_kz part[kz] + beta C over ksplit partials part[(kz N + j) M + i], fixed order.
+cudaError_t splitk_reduce(int M, int N, int ksplit, double2 alpha, const double2* part, double2 beta, double2* C,
+                          long ldc, cudaStream_t s);
 // In-place lower Cholesky of an n x n Hermitian matrix (column-major, lower
 // triangle used and overwritten, upper set to 0). *d_status = 1 on a
 // non-positive pivot.

@@ -256,17 +256,16 @@ cudaError_t gemm(int opA, int opB, int M, int N, int K, double2 alpha, const dou
                                 batch, ws, ws_elems, s, structure);
 }
 
-cudaError_t gemm_c64(int opA, int opB, int M, int N, int K, double2 alpha, const float2* A, long lda, const float2* B,
-                     long ldb, double2 beta, double2* C, long ldc, double2* ws, size_t ws_elems, cudaStream_t s,
-                     int structure) {
-  return gemm_impl<float, float2>(opA, opB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1, ws, ws_elems, s,
-                                  structure);
-}
-
 template cudaError_t gemm<double>(int, int, int, int, int, double2, const double2*, long, long, const double2*, long,
                                   long, double2, double2*, long, long, int, double2*, size_t, cudaStream_t, int);
-template cudaError_t gemm<float>(int, int, int, int, int, double2, const double2*, long, long, const double2*, long,
-                                 long, double2, double2*, long, long, int, double2*, size_t, cudaStream_t, int);
+
+cudaError_t splitk_reduce(int M, int N, int ksplit, double2 alpha, const double2* part, double2 beta, double2* C,
+                          long ldc, cudaStream_t s) {
+  const long total = (long)M * N;
+  const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+  k_splitk_reduce<<<blocks, 256, 0, s>>>(M, N, 1, ksplit, GEMM_GENERAL, alpha, part, beta, C, ldc, 0); launched();
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // Cholesky, right-looking, one column per pair of launches (pivot, update).

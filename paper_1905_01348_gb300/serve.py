@@ -22,6 +22,18 @@ reports the largest difference.
 prints one JSON object: per-step latency p50 / p99 over all steps of all
 requests, queueing delay, aggregate simulated fs per day and pair solves per
 second, the peak number of concurrent requests and the peak admitted bytes.
+
+Continuous batching (`BatchedServer`, the default of the command line): admitted
+requests of the same workload (grid) step together as one batch (pt_batch_step):
+their SCF iterations interleave on their own streams and the pair tiles of all
+their exchanges share launch groups replayed from a CUDA graph. Each workload
+group has a worker thread that advances its running requests one PT-CN step per
+tick; a request admitted while the group runs joins at the next tick, a finished
+one leaves at the end of its last tick (the batch is rebuilt when the set
+changes). Groups of different workloads run side by side. The pair-tile edge and
+launch-group size of each workload's batches come from the autotuner's table
+(tuning.json). `--per-request` runs every request on its own thread and stream
+instead, with no shared launches.
 """
 from __future__ import annotations
 
@@ -172,6 +184,176 @@ class Server:
         return [out[r.rid] for r in reqs]
 
 
+class BatchedServer:
+    """Continuous batching: admitted requests of one group (workload) step together.
+
+    footprint(req) and open_system(req, slot) as for Server; make_batch(systems) -> an
+    object with step() -> (status, [info dict per system]) and close(); group_of(req)
+    -> the group key (requests of one group must be able to share a batch). Systems are
+    opened on their own threads (start-state relaxation can take seconds) and join their
+    group's running batch at the next tick.
+    """
+
+    def __init__(self, footprint, open_system, make_batch, budget_bytes: int, max_active: int = 8,
+                 keep_orbitals: bool = False, clock=time.perf_counter, group_of=lambda r: r.workload):
+        if max_active < 1:
+            raise ValueError("max_active must be >= 1")
+        self.footprint = footprint
+        self.open_system = open_system
+        self.make_batch = make_batch
+        self.budget = int(budget_bytes)
+        self.max_active = int(max_active)
+        self.keep_orbitals = keep_orbitals
+        self.clock = clock
+        self.group_of = group_of
+        self.peak_active = 0
+        self.peak_bytes = 0
+        self.peak_batch = 0
+        self.ticks = 0
+        self.wall_s = 0.0
+
+    def run(self, requests) -> list:
+        reqs = list(requests)
+        out = {r.rid: Outcome(r.rid, r.workload, int(self.footprint(r)), r.arrival_s) for r in reqs}
+        pending = collections.deque(sorted(reqs, key=lambda r: (r.arrival_s, r.rid)))
+        cv = threading.Condition()
+        free_slots = list(range(self.max_active - 1, -1, -1))
+        used = [0]
+        active = [0]
+        ready = collections.defaultdict(list)       # group -> [(req, outcome, system)] opened, not yet stepping
+        groups = {}                                  # group -> worker thread
+        threads = []
+        t0 = self.clock()
+
+        def release(o):
+            # with cv held
+            o.finished_s = self.clock() - t0
+            used[0] -= o.footprint
+            active[0] -= 1
+            free_slots.append(o.slot)
+            cv.notify_all()
+
+        def close_quietly(o, system):
+            try:
+                system.close()
+            except Exception as e:
+                o.error = o.error or f"close: {type(e).__name__}: {e}"
+
+        def opener(req, o):
+            try:
+                system = self.open_system(req, o.slot)
+            except Exception as e:
+                o.error = f"{type(e).__name__}: {e}"
+                with cv:
+                    release(o)
+                return
+            with cv:
+                ready[self.group_of(req)].append((req, o, system))
+                cv.notify_all()
+
+        def worker(key):
+            running = []      # [req, outcome, system, steps done]
+            batch, members = None, ()
+            while True:
+                with cv:
+                    while not ready[key] and not running:
+                        # nothing to step: wait for a request of this group, or finish when none can come
+                        more = any(self.group_of(r) == key for r in pending) or any(
+                            out[r.rid].admitted_s is not None and out[r.rid].finished_s is None and
+                            self.group_of(r) == key for r in reqs)
+                        if not more:
+                            groups.pop(key, None)
+                            cv.notify_all()
+                            return
+                        cv.wait(timeout=0.05)
+                    for req, o, system in ready[key]:
+                        running.append([req, o, system, 0])
+                    ready[key].clear()
+                ids = tuple(id(x[2]) for x in running)
+                try:
+                    if ids != members:
+                        if batch is not None:
+                            batch.close()
+                        batch = self.make_batch([x[2] for x in running])
+                        members = ids
+                    t = self.clock()
+                    _, infos = batch.step()
+                    dt_ms = (self.clock() - t) * 1e3
+                except Exception as e:   # the whole group fails this tick; every member is reported
+                    msg = f"{type(e).__name__}: {e}"
+                    with cv:
+                        for req, o, system, _ in running:
+                            o.error = msg
+                            close_quietly(o, system)
+                            release(o)
+                    running, batch, members = [], None, ()
+                    continue
+                with cv:
+                    self.ticks += 1
+                    self.peak_batch = max(self.peak_batch, len(running))
+                    keep = []
+                    for x, info in zip(running, infos):
+                        req, o, system, k = x
+                        o.step_ms.append(dt_ms)
+                        o.energy.append(info["energy"])
+                        o.dipole.append(list(info["dipole"]))
+                        o.scf_iters.append(info["scf_iters"])
+                        x[3] = k + 1
+                        if x[3] >= req.steps:
+                            if self.keep_orbitals:
+                                o.orbitals = system.orbitals()
+                            close_quietly(o, system)
+                            release(o)
+                        else:
+                            keep.append(x)
+                    running = keep
+                if not running and batch is not None:
+                    batch.close()
+                    batch, members = None, ()
+
+        with cv:
+            while pending or active[0]:
+                now = self.clock() - t0
+                while pending and pending[0].arrival_s <= now and free_slots:
+                    r = pending[0]
+                    o = out[r.rid]
+                    if o.footprint > self.budget:
+                        o.error = f"footprint {o.footprint} B exceeds the budget {self.budget} B"
+                        pending.popleft()
+                        continue
+                    if used[0] + o.footprint > self.budget:
+                        break
+                    pending.popleft()
+                    o.slot = free_slots.pop()
+                    o.admitted_s = now
+                    used[0] += o.footprint
+                    active[0] += 1
+                    self.peak_active = max(self.peak_active, active[0])
+                    self.peak_bytes = max(self.peak_bytes, used[0])
+                    if r.steps < 1:
+                        release(o)
+                        continue
+                    th = threading.Thread(target=opener, args=(r, o), daemon=True)
+                    threads.append(th)
+                    th.start()
+                    key = self.group_of(r)
+                    if key not in groups:
+                        g = threading.Thread(target=worker, args=(key,), daemon=True)
+                        groups[key] = g
+                        threads.append(g)
+                        g.start()
+                if not pending and not active[0]:
+                    break
+                timeout = 0.05
+                if pending and pending[0].arrival_s > now:
+                    timeout = min(timeout, pending[0].arrival_s - now)
+                cv.wait(timeout=timeout)
+        for th in threads:
+            th.join()
+        self.wall_s = self.clock() - t0
+        return [out[r.rid] for r in reqs]
+
+
 def summarize(outcomes, wall_s: float, dt_au: float, pairs_of) -> dict:
     """Latency and throughput of a served run. pairs_of(workload) = pair solves per step."""
     steps = [ms for o in outcomes for ms in o.step_ms]
@@ -188,6 +370,31 @@ def summarize(outcomes, wall_s: float, dt_au: float, pairs_of) -> dict:
         "fs_per_day": fs / wall_s * 86400.0 if wall_s > 0 else None,
         "pair_solves_per_s": pairs / wall_s if wall_s > 0 else None,
     }
+
+
+def tuned_batch_shape(workload: str, precision: str, path: str | None = None) -> dict:
+    """Pair-tile edge and launch-group size for batches of a workload, from the
+    autotuner's table (tuning.json next to this module); automatic when absent."""
+    import os
+    if path is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+    try:
+        with open(path) as f:
+            best = json.load(f)[f"{workload}-{precision}"]["best"]
+        return {"pair_tile": int(best["pair_tile"]), "tiles_per_launch": int(best["tiles_per_launch"])}
+    except (OSError, KeyError, ValueError, TypeError):
+        return {"pair_tile": 0, "tiles_per_launch": 0}
+
+
+def cuda_batch_factory():
+    """make_batch(systems) for BatchedServer: a pt_batch over the systems with the tuned shape."""
+    from .system import Batch
+
+    def make_batch(systems):
+        shape = tuned_batch_shape(systems[0].workload, systems[0].precision)
+        return Batch(systems, pair_tile=shape["pair_tile"], tiles_per_launch=shape["tiles_per_launch"])
+
+    return make_batch
 
 
 def cuda_backend(device: str = "cuda:0", max_active: int = 8):
@@ -215,7 +422,9 @@ def cuda_backend(device: str = "cuda:0", max_active: int = 8):
         g2 = syn.basis_g2(nat.pt_basis_indices(p), w["n"], w["cell"])
         c0 = syn.initial_coefficients(g2, w["n_orb"], seed=req.seed)
         with torch.cuda.stream(streams[slot]):
-            return System(w, c0, device=str(dev), stream=streams[slot])
+            system = System(w, c0, device=str(dev), stream=streams[slot])
+        system.workload, system.precision = req.workload, req.precision
+        return system
 
     return footprint, open_system
 
@@ -235,6 +444,8 @@ def main(argv=None) -> None:
                     help="12 Si8 + 12 Si64 trajectories, all at t = 0, 20 steps, kicks from seed 1")
     ap.add_argument("--check-alone", action="store_true",
                     help="re-run every request alone and report the largest difference of its results")
+    ap.add_argument("--per-request", action="store_true",
+                    help="every request on its own thread and stream (no batching of pair launches)")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -252,13 +463,21 @@ def main(argv=None) -> None:
                 for d in stream]
     budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else int(0.9 * torch.cuda.mem_get_info()[0])
     footprint, open_system = cuda_backend(max_active=args.max_active)
-    srv = Server(footprint, open_system, budget, args.max_active, keep_orbitals=args.check_alone)
+    if args.per_request:
+        srv = Server(footprint, open_system, budget, args.max_active, keep_orbitals=args.check_alone)
+    else:
+        srv = BatchedServer(footprint, open_system, cuda_batch_factory(), budget, args.max_active,
+                            keep_orbitals=args.check_alone)
     outs = srv.run(reqs)
     n_orb = {k: syn.si_workload(k)["n_orb"] for k in ("si8", "si64", "si216")}
     res = summarize(outs, srv.wall_s, syn.DT_50AS, lambda wl: n_orb[wl] * (n_orb[wl] + 1) // 2)
     res.update({"mode": "batched" if args.batched else "poisson", "rate_per_s": None if args.batched else args.rate,
                 "precision": args.precision, "max_active": args.max_active, "budget_bytes": budget,
-                "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes})
+                "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes,
+                "scheduling": "per-request" if args.per_request else "continuous batching",
+                **({} if args.per_request else {"peak_batch": srv.peak_batch, "ticks": srv.ticks,
+                                                "batch_shape": {w: tuned_batch_shape(w, args.precision)
+                                                                for w in sorted({r.workload for r in reqs})}})})
     if args.check_alone:
         alone = Server(footprint, open_system, budget, 1, keep_orbitals=True)
         worst_psi, worst_e = 0.0, 0.0

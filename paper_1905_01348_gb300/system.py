@@ -92,3 +92,46 @@ class System:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Several systems stepped together (pt_batch_*): their pair tiles share launch groups.
+
+    systems: System objects with the same grid, precision, cell, cutoff and kernel; each
+    keeps its own stream. The batch workspace and the stream of the merged pair kernels
+    come from PyTorch. pair_tile / tiles_per_launch: the tile edge and launch-group size
+    (0: automatic; the autotuner's table gives tuned values).
+    """
+
+    def __init__(self, systems, pair_tile: int = 0, tiles_per_launch: int = 0):
+        import torch
+        self.torch = torch
+        self.systems = list(systems)
+        dev = self.systems[0].device
+        handles = [s.handle for s in self.systems]
+        self.ws_bytes = nat.pt_batch_workspace_size(handles, pair_tile, tiles_per_launch)
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.Stream(dev)
+        self.handle = nat.pt_batch_create(handles, pair_tile, tiles_per_launch, self.workspace.data_ptr(),
+                                          self.ws_bytes, self.stream.cuda_stream)
+
+    def step(self):
+        """One PT-CN step of every system: (status, [step info per system])."""
+        return nat.pt_batch_step(self.handle, len(self.systems))
+
+    def exchange(self):
+        """V_X Psi of every system's current orbitals, one (n_orb, npw) complex128 device tensor each."""
+        outs = [self.torch.empty((s.n_orb, s.npw), dtype=self.torch.complex128, device=s.device) for s in self.systems]
+        nat.pt_batch_exchange(self.handle, [o.data_ptr() for o in outs])
+        return outs
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None:
+            nat.pt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

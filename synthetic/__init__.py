@@ -69,6 +69,9 @@ COMMON = dict(
     scf_tol=1e-6,
     scf_max=50,
     scf_fixed_iters=0,
+    # mixed precision: below this SCF tolerance the late iterations run in FP64
+    # (no effect at the paper's tolerance 1e-6)
+    scf_fp64_below=1e-7,
 )
 
 

@@ -44,3 +44,25 @@ def test_mix_equals_alone(pkg):
         assert np.array_equal(a.orbitals, o.orbitals)
         assert a.energy == o.energy and a.dipole == o.dipole
     assert not np.array_equal(mix[0].orbitals, mix[1].orbitals)
+
+
+def test_continuous_batching_equals_alone(pkg):
+    """Continuous batching: Si8 requests arriving 30 ms apart join one batch (shared pair
+    launches, interleaved SCF iterations) and leave it as they finish; each must match the
+    same request run alone on the per-request path, bit for bit (same pair tile, 4)."""
+    from paper_1905_01348_gb300.serve import BatchedServer, Request, Server, cuda_backend
+    kicks = syn.batched_kicks(3, seed=1)
+    reqs = [Request(k, "si8", 2 + k, 0.03 * k, seed=k, kick=tuple(kicks[k])) for k in range(3)]
+    footprint, open_system = cuda_backend(max_active=3)
+    budget = 3 * max(footprint(r) for r in reqs)
+    srv = BatchedServer(footprint, open_system, lambda systems: pkg.Batch(systems, pair_tile=4), budget,
+                        max_active=3, keep_orbitals=True)
+    mix = srv.run(reqs)
+    assert srv.peak_batch >= 2
+    for r, o in zip(reqs, mix):
+        assert o.error is None, o.error
+        (a,) = Server(footprint, open_system, budget, 1, keep_orbitals=True).run([dataclasses.replace(r, arrival_s=0.0)])
+        assert a.error is None, a.error
+        assert len(o.energy) == r.steps
+        assert np.array_equal(a.orbitals, o.orbitals)
+        assert a.energy == o.energy and a.dipole == o.dipole

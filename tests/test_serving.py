@@ -4,7 +4,11 @@ Checked: admission in arrival order by footprint and free slots (never over the
 budget, never more than max_active at once), requests that arrive while others
 run are admitted as soon as memory frees up, oversized and failing requests are
 reported without stopping the others, and every request gets its own results
-back whatever the mix (a stand-in that steps an oracle model per request).
+back whatever the mix (a stand-in that steps an oracle model per request). The
+continuous-batching server is checked the same way with a stand-in batch that
+steps its members in order: requests of one workload share ticks, a request that
+arrives while a batch runs joins it at a later tick, groups of different
+workloads are batched apart, and a failing batch reports every member.
 """
 import os
 import threading
@@ -14,7 +18,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
-from paper_1905_01348_gb300.serve import Request, Server, percentile, summarize
+from paper_1905_01348_gb300.serve import BatchedServer, Request, Server, percentile, summarize
 
 
 class SleepSystem:
@@ -199,10 +203,21 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
         def close(self):
             pass
 
+    class FakeBatch:
+        def __init__(self, systems, pair_tile=0, tiles_per_launch=0):
+            self.systems = systems
+
+        def step(self):
+            return 0, [x.step()[1] for x in self.systems]
+
+        def close(self):
+            pass
+
     monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
     monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
     monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
     monkeypatch.setattr(system_mod, "System", FakeSystem)
+    monkeypatch.setattr(system_mod, "Batch", FakeBatch)
 
     serve.main(["--batched", "--budget-gb", "1000", "--max-active", "4", "--check-alone"])
     res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -215,8 +230,78 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     assert sum(s.params["n_orb"] == 16 for s in firsts) == 12
     assert all(s.params["precision"] == "mixed" and s.params["fock_mode"] == "ace" for s in firsts)
 
+    assert res["scheduling"] == "continuous batching" and res["peak_batch"] >= 2
+
     made.clear()
     serve.main(["--requests", "5", "--rate", "50", "--steps-max", "6", "--workloads", "si8,si64",
                 "--budget-gb", "1000"])
     res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert res["mode"] == "poisson" and res["completed"] == 5 and res["step_latency_ms"]["p99"] is not None
+    serve.main(["--requests", "3", "--rate", "50", "--steps-max", "6", "--budget-gb", "1000", "--per-request"])
+    res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert res["scheduling"] == "per-request" and res["completed"] == 3
+
+
+class SeqBatch:
+    """Stand-in for a pt_batch: steps its member systems in order; records its members."""
+    made = []
+
+    def __init__(self, systems, fail=False):
+        self.systems = list(systems)
+        self.fail = fail
+        SeqBatch.made.append(tuple(x.req.rid for x in self.systems if hasattr(x, "req")))
+
+    def step(self):
+        if self.fail:
+            raise RuntimeError("planted batch failure")
+        out = [x.step() for x in self.systems]
+        return 0, [info for _, info in out]
+
+    def close(self):
+        pass
+
+
+def test_batched_server_joins_and_groups():
+    reset_counts()
+    SeqBatch.made.clear()
+    reqs = [Request(0, "si8", 12, 0.0), Request(1, "si8", 3, 0.0), Request(2, "si64", 4, 0.0),
+            Request(3, "si8", 3, 0.05)]
+    srv = BatchedServer(lambda r: 1, lambda r, s: SleepSystem(r, s), SeqBatch, budget_bytes=10, max_active=4)
+    outs = srv.run(reqs)
+    assert all(o.error is None and len(o.step_ms) == r.steps for r, o in zip(reqs, outs))
+    assert SleepSystem.open_now == 0 and srv.peak_active <= 4
+    groups = {frozenset(m) for m in SeqBatch.made}
+    # si8 and si64 requests are never in one batch; 0 and 1 step together; 3 joins 0 later
+    assert all(not ({0, 1, 3} & g and 2 in g) for g in groups)
+    assert any({0, 1} <= g for g in groups) and any({0, 3} <= g for g in groups)
+    assert outs[3].admitted_s < outs[0].finished_s
+    assert srv.peak_batch >= 2 and srv.ticks >= 12
+    # every member of a tick sees that tick's latency: request 1's ticks all carried request 0
+    assert set(outs[1].step_ms) <= set(outs[0].step_ms)
+
+
+def test_batched_server_budget_and_failure():
+    reset_counts()
+    sizes = {0: 60, 1: 60, 2: 30}
+    reqs = [Request(k, "si8", 3, 0.0) for k in range(3)]
+    srv = BatchedServer(lambda r: sizes[r.rid], lambda r, s: SleepSystem(r, s), SeqBatch, budget_bytes=100,
+                        max_active=3)
+    outs = srv.run(reqs)
+    assert srv.peak_bytes <= 100 and all(o.error is None for o in outs)
+    assert outs[1].admitted_s >= outs[0].finished_s - 1e-6      # 1 waits for memory
+    reset_counts()
+    failing = BatchedServer(lambda r: 1, lambda r, s: SleepSystem(r, s), lambda xs: SeqBatch(xs, fail=True),
+                            budget_bytes=10, max_active=2)
+    outs = failing.run([Request(k, "si8", 2, 0.0) for k in range(2)])
+    assert all("planted batch failure" in o.error for o in outs) and SleepSystem.open_now == 0
+
+
+def test_batched_results_are_the_same_alone_and_in_the_mix():
+    kicks = syn.batched_kicks(4, seed=1)
+    reqs = [Request(k, "si8", 2 + k % 2, 0.01 * k, seed=k, kick=tuple(kicks[k])) for k in range(4)]
+    mix = BatchedServer(lambda r: 1, OracleSystem, SeqBatch, budget_bytes=3, max_active=3,
+                        keep_orbitals=True).run(reqs)
+    for r, o in zip(reqs, mix):
+        (a,) = Server(lambda r: 1, OracleSystem, budget_bytes=3, max_active=1, keep_orbitals=True).run([r])
+        assert o.error is None and a.error is None
+        assert np.array_equal(a.orbitals, o.orbitals) and a.energy == o.energy
