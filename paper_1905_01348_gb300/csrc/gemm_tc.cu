@@ -47,13 +47,15 @@ constexpr int TC_NC = 128;           // complex output columns per tile (256 rea
 constexpr int TC_KC = 8;             // complex k per stage (16 real k: two MMAs of K = 8)
 constexpr int TC_NS = 2;             // ring stages
 constexpr int TC_WIN = 8;            // stages per accumulation window (48 MMAs)
-constexpr int TC_PROD = 128;         // producer / epilogue threads (warps 0-3)
-constexpr int TC_THREADS = 160;      // + warp 4: tensor-memory allocation and MMA issue
+constexpr int TC_PF = 4;             // stages of operand loads in flight per producer thread
+static_assert(TC_WIN % TC_PF == 0, "the producer loop steps through windows in groups of TC_PF stages");
+constexpr int TC_PROD = 256;         // producer / drain threads (warps 0-7), two per tile row
+constexpr int TC_THREADS = 288;      // + warp 8: tensor-memory allocation and MMA issue
 constexpr uint32_t TC_TMEM_COLS = 512;                      // two accumulators of 256 columns
 constexpr uint32_t A_BYTES = TC_M * 2 * TC_KC * 4;           // 128 rows x 16 floats
 constexpr uint32_t B_BYTES = 2 * TC_NC * 2 * TC_KC * 4;      // 256 rows x 16 floats
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // [A hi][A lo][B hi][B lo]
-constexpr uint32_t SUM_BYTES = 2 * TC_NC * TC_M * 4;         // FP32 window sums, [column][row]
+constexpr uint32_t SUM_BYTES = 2 * TC_NC * TC_M * 4;         // FP32 window sums, [256 columns][128 rows]
 constexpr uint32_t TC_SMEM = TC_NS * STAGE_BYTES + SUM_BYTES;  // 224 KB: one CTA per SM
 constexpr long long kWaitCycles = 4000000000LL;              // about 2 s at 2 GHz
 
@@ -64,6 +66,7 @@ constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 *
                             ((uint32_t)TC_M >> 4 << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 
 // Shared-memory matrix descriptor, K-major without swizzle: the 8 x 16-byte core
 // matrices are 128 contiguous bytes; LBO = 128 bytes to the next core matrix along K,
@@ -164,11 +167,17 @@ __device__ __forceinline__ uint32_t core_off(int r, int kc) {
 // (and k < n0 + 128 when op(B) is upper triangular). ksplit > 1: the raw sums go to
 // part[(kz N + j) M + i]; otherwise C = alpha sum + beta C.
 //
+// Threads: warps 0-7 produce and drain, two threads per tile row r = 32 (w % 4) + lane
+// (warp w reaches TMEM lanes 32 (w % 4)..+31); thread half h = w / 4 loads and converts
+// complex k 4h..4h+3 of each stage (TC_PF stages ahead, in registers) and owns
+// accumulator columns 128h..128h+127 (C_r for h = 0, C_i for h = 1). Warp 8 allocates
+// tensor memory and one of its threads issues the MMAs.
+//
 // Accumulation. The tensor core adds into its FP32 accumulator with truncation, so its
 // error grows linearly with the number of MMAs into one accumulator (measured: 4e-5
 // relative after 2250 MMAs). Each window of TC_WIN stages (48 MMAs) therefore starts a
-// fresh accumulator, and the producer warps add the finished window into FP32 sums in
-// shared memory (round to nearest), one slice of columns after each stage they
+// fresh accumulator, and the producer threads add the finished window into FP32 sums in
+// shared memory (round to nearest), one slice of 16 columns after each stage they
 // produce. Two TMEM accumulators alternate, so the MMAs of window w run while window
 // w - 1 is drained.
 template <int OPA, int OPB>
@@ -188,6 +197,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   int kend = min(K, kbeg + kchunk);
   if (tri_b) kend = min(kend, n0 + TC_NC);
   const int nst = kend > kbeg ? (kend - kbeg + TC_KC - 1) / TC_KC : 0;
+  const int nwin = (nst + TC_WIN - 1) / TC_WIN;
   float* sums = reinterpret_cast<float*>(smem + TC_NS * STAGE_BYTES);   // [256 columns][128 rows]
 
   if (tid == 0) {
@@ -202,7 +212,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
-  if (warp == 4) {
+  if (warp == TC_PROD / 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
                  "r"(TC_TMEM_COLS)
                  : "memory");
@@ -214,70 +224,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = tmem_base;
   bool ok = true;
 
-  if (warp < 4) {
-    // ---- producer: row m0 + tid of op(A), column n0 + tid of op(B); then the drains ----
-    const int t = tid;
-    const int m = m0 + t, n = n0 + t;
-    const uint32_t trow = (uint32_t)(32 * warp) << 16;   // this warp's TMEM lane quarter
-    float2 av[TC_KC], bv[TC_KC];
-    auto load = [&](int st) {
-      const int kb = kbeg + st * TC_KC;
+  if (warp < TC_PROD / 32) {
+    const int q = warp & 3, h = warp >> 2;
+    const int r = 32 * q + lane;                 // tile row of op(A), tile column of op(B)
+    const int m = m0 + r, n = n0 + r;
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
+    float* my_sums = sums + (TC_NC * h) * TC_M + r;   // column j of this thread: my_sums[j * TC_M]
+    float2 pa[TC_PF][4], pb[TC_PF][4];           // stages st .. st + TC_PF - 1 in flight (buffer st % TC_PF)
+    auto load = [&](int st, float2 (&a)[4], float2 (&b)[4]) {
+      const int kb = kbeg + st * TC_KC + 4 * h;
 #pragma unroll
-      for (int k = 0; k < TC_KC; ++k) {
-        const int kk = kb + k;
-        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-        if (m < M && kk < kend) {
-          if (OPA == OP_N) a = __ldg(A + m + (long)kk * lda);
-          else { a = __ldg(A + kk + (long)m * lda); a.y = -a.y; }
+      for (int j = 0; j < 4; ++j) {
+        const int kk = kb + j;
+        float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+        if (st < nst && m < M && kk < kend) {
+          if (OPA == OP_N) va = __ldg(A + m + (long)kk * lda);
+          else { va = __ldg(A + kk + (long)m * lda); va.y = -va.y; }
         }
-        if (n < N && kk < kend) {
-          if (OPB == OP_N) b = __ldg(B + kk + (long)n * ldb);
-          else { b = __ldg(B + n + (long)kk * ldb); b.y = -b.y; }
+        if (st < nst && n < N && kk < kend) {
+          if (OPB == OP_N) vb = __ldg(B + kk + (long)n * ldb);
+          else { vb = __ldg(B + n + (long)kk * ldb); vb.y = -vb.y; }
         }
-        av[k] = a;
-        bv[k] = b;
+        a[j] = va;
+        b[j] = vb;
       }
     };
-    // slices [s0, s1) of window win's accumulator into the FP32 sums of this thread's row
-    auto drain = [&](int win, int s0, int s1) {
-      if (s0 >= s1) return;
-      const int b = win & 1;
-      if (s0 == 0 && ok) ok = mbar_wait(&bar_acc_full[b], (uint32_t)(win >> 1) & 1u, err);
-      tc_fence_after();
-      // tcgen05.ld is warp-collective: the whole warp reads the accumulator, or none of it
-      const bool rd = __all_sync(0xffffffffu, ok);
-      constexpr int SW = 2 * TC_NC / TC_WIN;   // columns per slice
-      for (int sl = s0; sl < s1; ++sl) {
-#pragma unroll
-        for (int c = sl * SW; c < (sl + 1) * SW; c += 16) {
-          uint32_t v[16];
-          if (rd) {
-            tmem_ld16(tmem + trow + (uint32_t)(b * 2 * TC_NC + c), v);
-            tmem_ld_wait();
-          } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0u;
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            float* sp = sums + (c + i) * TC_M + t;
-            *sp = win == 0 ? __uint_as_float(v[i]) : *sp + __uint_as_float(v[i]);
-          }
-        }
-      }
-      if (s1 == TC_WIN) {
-        tc_fence_before();
-        mbar_arrive(&bar_acc_empty[b]);
-      }
-    };
-    if (nst > 0) load(0);
-    for (int st = 0; st < nst; ++st) {
+    // store stage st (from a, b) into its ring slot
+    auto produce = [&](int st, const float2 (&a)[4], const float2 (&b)[4]) {
       const int s = st % TC_NS;
       const uint32_t ph = (uint32_t)(st / TC_NS) & 1u;
-      float2 ac[TC_KC], bc[TC_KC];
-#pragma unroll
-      for (int k = 0; k < TC_KC; ++k) { ac[k] = av[k]; bc[k] = bv[k]; }
-      if (st + 1 < nst) load(st + 1);   // next stage in flight while this one is stored
       if (ok) ok = mbar_wait(&bar_empty[s], ph ^ 1u, err);
       unsigned char* Ahi = smem + s * STAGE_BYTES;
       unsigned char* Alo = Ahi + A_BYTES;
@@ -285,48 +260,83 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       unsigned char* Blo = Bhi + B_BYTES;
       if (ok) {
 #pragma unroll
-        for (int kc = 0; kc < 4; ++kc) {
-          const float2 a0 = ac[2 * kc], a1 = ac[2 * kc + 1];
-          const float2 b0 = bc[2 * kc], b1 = bc[2 * kc + 1];
-          st_split(Ahi, Alo, core_off(t, kc), a0.x, a0.y, a1.x, a1.y);
-          st_split(Bhi, Blo, core_off(t, kc), b0.x, -b0.y, b1.x, -b1.y);          // -> C_r
-          st_split(Bhi, Blo, core_off(t + TC_NC, kc), b0.y, b0.x, b1.y, b1.x);    // -> C_i
+        for (int c = 0; c < 2; ++c) {   // core-matrix columns kc = 2h + c: complex k 4h + 2c, +1
+          const int kc = 2 * h + c;
+          const float2 a0 = a[2 * c], a1 = a[2 * c + 1], b0 = b[2 * c], b1 = b[2 * c + 1];
+          st_split(Ahi, Alo, core_off(r, kc), a0.x, a0.y, a1.x, a1.y);
+          st_split(Bhi, Blo, core_off(r, kc), b0.x, -b0.y, b1.x, -b1.y);          // -> C_r
+          st_split(Bhi, Blo, core_off(r + TC_NC, kc), b0.y, b0.x, b1.y, b1.x);    // -> C_i
         }
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_arrive(&bar_full[s]);
-      // one slice of the previous window per stage of this one
-      const int win = st / TC_WIN, pos = st % TC_WIN;
-      if (win >= 1) drain(win - 1, pos, pos + 1);
+    };
+    // slice pos (16 columns) of window dw's accumulator into the sums
+    auto drain = [&](int dw, int pos) {
+      const int b = dw & 1;
+      if (pos == 0 && ok) ok = mbar_wait(&bar_acc_full[b], (uint32_t)(dw >> 1) & 1u, err);
+      tc_fence_after();
+      uint32_t v[16];
+      // tcgen05.ld is warp-collective: the whole warp reads the accumulator, or none of it
+      if (__all_sync(0xffffffffu, ok)) {
+        tmem_ld16(tmem + tlane + (uint32_t)(b * 2 * TC_NC + TC_NC * h + 16 * pos), v);
+        tmem_ld_wait();
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0u;
+      }
+      float* sp = my_sums + (16 * pos) * TC_M;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sp[i * TC_M] = dw == 0 ? __uint_as_float(v[i]) : sp[i * TC_M] + __uint_as_float(v[i]);
+      if (pos == TC_WIN - 1) {
+        tc_fence_before();
+        mbar_arrive(&bar_acc_empty[b]);
+      }
+    };
+#pragma unroll
+    for (int e = 0; e < TC_PF; ++e) load(e, pa[e], pb[e]);
+    // stages in groups of TC_PF (stage st in buffer st % TC_PF); after producing stage
+    // st = TC_WIN win + pos, drain slice pos of window win - 1
+#pragma unroll 1
+    for (int st0 = 0; st0 < TC_WIN * (nwin + 1); st0 += TC_PF) {
+#pragma unroll
+      for (int e = 0; e < TC_PF; ++e) {
+        const int st = st0 + e;
+        if (st < nst) {
+          float2 a[4], b[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) { a[j] = pa[e][j]; b[j] = pb[e][j]; }
+          load(st + TC_PF, pa[e], pb[e]);   // TC_PF stages ahead, in flight while this one is stored
+          produce(st, a, b);
+        }
+        const int win = st / TC_WIN, pos = st % TC_WIN;
+        if (win >= 1 && win - 1 < nwin) drain(win - 1, pos);
+      }
     }
-    if (nst > 0) {
-      const int last = (nst - 1) / TC_WIN, pos = (nst - 1) % TC_WIN;
-      if (last >= 1) drain(last - 1, pos + 1, TC_WIN);
-      drain(last, 0, TC_WIN);
-    }
-    // ---- output: this thread's row of the tile ----------------------------------
+    // ---- output ----------------------------------------------------------------------
+    asm volatile("bar.sync 1, %0;\n" ::"r"(TC_PROD) : "memory");   // both halves of every row drained
     if (m < M) {
-      for (int j0 = 0; j0 < TC_NC; ++j0) {
+      for (int j0 = (TC_NC / 2) * h; j0 < (TC_NC / 2) * (h + 1); ++j0) {
         const int j = n0 + j0;
         if (j >= N) break;
         double2 v = make_double2(0.0, 0.0);
-        if (nst > 0) v = make_double2((double)sums[j0 * TC_M + t], (double)sums[(TC_NC + j0) * TC_M + t]);
+        if (nst > 0) v = make_double2((double)sums[j0 * TC_M + r], (double)sums[(TC_NC + j0) * TC_M + r]);
         if (ksplit > 1) {
           part[((long)kz * N + j) * (long)M + m] = v;
         } else {
           double2* c = Cm + m + (long)j * ldc;
-          double2 r = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
+          double2 o2 = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
           if (beta.x != 0.0 || beta.y != 0.0) {
             const double2 o = *c;
-            r.x += beta.x * o.x - beta.y * o.y;
-            r.y += beta.x * o.y + beta.y * o.x;
+            o2.x += beta.x * o.x - beta.y * o.y;
+            o2.y += beta.x * o.y + beta.y * o.x;
           }
-          *c = r;
+          *c = o2;
         }
       }
     }
   } else if (lane == 0) {
-    // ---- MMA issue (one thread of warp 4) --------------------------------------------
+    // ---- MMA issue (one thread of warp 8) --------------------------------------------
     const uint32_t sbase = smem_u32(smem);
     for (int st = 0; st < nst; ++st) {
       const int s = st % TC_NS;
@@ -339,21 +349,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t d = tmem + (uint32_t)(b * 2 * TC_NC);
         const uint32_t ahi = sbase + s * STAGE_BYTES, alo = ahi + A_BYTES, bhi = alo + A_BYTES, blo = bhi + B_BYTES;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {   // K = 8 real values = two core matrices along K
-          const uint32_t o = q * 256;
-          tc_mma(d, smem_desc(ahi + o), smem_desc(bhi + o), (pos > 0 || q > 0) ? 1u : 0u);
+        for (int qq = 0; qq < 2; ++qq) {   // K = 8 real values = two core matrices along K
+          const uint32_t o = qq * 256;
+          tc_mma(d, smem_desc(ahi + o), smem_desc(bhi + o), (pos > 0 || qq > 0) ? 1u : 0u);
           tc_mma(d, smem_desc(ahi + o), smem_desc(blo + o), 1u);
           tc_mma(d, smem_desc(alo + o), smem_desc(bhi + o), 1u);
         }
       }
-      tc_commit(&bar_empty[s]);                                    // stage s is free once read
+      tc_commit(&bar_empty[s]);                                            // stage s is free once read
       if (pos == TC_WIN - 1 || st == nst - 1) tc_commit(&bar_acc_full[b]);   // window complete
     }
   }
-  if (warp == 4) __syncwarp();
+  if (warp == TC_PROD / 32) __syncwarp();
   tc_fence_before();
   __syncthreads();
-  if (warp == 4) {
+  if (warp == TC_PROD / 32) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }

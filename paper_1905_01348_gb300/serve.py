@@ -30,9 +30,12 @@ their exchanges share launch groups replayed from a CUDA graph. Each workload
 group has a worker thread that advances its running requests one PT-CN step per
 tick; a request admitted while the group runs joins at the next tick, a finished
 one leaves at the end of its last tick (the batch is rebuilt when the set
-changes). Groups of different workloads run side by side. The pair-tile edge and
-launch-group size of each workload's batches come from the autotuner's table
-(tuning.json). `--per-request` runs every request on its own thread and stream
+changes). Groups of different workloads run side by side. Workloads whose own
+exchange already fills the GPU (Si216) are not batched: each such request is a
+group of its own. The pair-tile edge and launch-group size of each workload's
+batches come from the autotuner's table (tuning.json), the launch-group size capped
+so that a batch's pair intermediate stays within 4 GiB, which the admission budget
+reserves while the group runs. `--per-request` runs every request on its own thread and stream
 instead, with no shared launches.
 """
 from __future__ import annotations
@@ -189,18 +192,22 @@ class BatchedServer:
 
     footprint(req) and open_system(req, slot) as for Server; make_batch(systems) -> an
     object with step() -> (status, [info dict per system]) and close(); group_of(req)
-    -> the group key (requests of one group must be able to share a batch). Systems are
-    opened on their own threads (start-state relaxation can take seconds) and join their
+    -> the group key (requests of one group must be able to share a batch);
+    group_reserve(key) -> device bytes a group's batch holds while the group runs, taken
+    from the budget when the group starts and returned when it ends. Systems are opened
+    on their own threads (start-state relaxation can take seconds) and join their
     group's running batch at the next tick.
     """
 
     def __init__(self, footprint, open_system, make_batch, budget_bytes: int, max_active: int = 8,
-                 keep_orbitals: bool = False, clock=time.perf_counter, group_of=lambda r: r.workload):
+                 keep_orbitals: bool = False, clock=time.perf_counter, group_of=lambda r: r.workload,
+                 group_reserve=lambda key: 0):
         if max_active < 1:
             raise ValueError("max_active must be >= 1")
         self.footprint = footprint
         self.open_system = open_system
         self.make_batch = make_batch
+        self.group_reserve = group_reserve    # bytes a group's batch holds while the group runs
         self.budget = int(budget_bytes)
         self.max_active = int(max_active)
         self.keep_orbitals = keep_orbitals
@@ -222,6 +229,7 @@ class BatchedServer:
         active = [0]
         ready = collections.defaultdict(list)       # group -> [(req, outcome, system)] opened, not yet stepping
         groups = {}                                  # group -> worker thread
+        reserved = {}                                # group -> bytes held for its batch
         threads = []
         t0 = self.clock()
 
@@ -263,6 +271,7 @@ class BatchedServer:
                             self.group_of(r) == key for r in reqs)
                         if not more:
                             groups.pop(key, None)
+                            used[0] -= reserved.pop(key, 0)
                             cv.notify_all()
                             return
                         cv.wait(timeout=0.05)
@@ -312,37 +321,40 @@ class BatchedServer:
                     batch, members = None, ()
 
         with cv:
-            while pending or active[0]:
+            while pending or active[0] or groups:
                 now = self.clock() - t0
                 while pending and pending[0].arrival_s <= now and free_slots:
                     r = pending[0]
                     o = out[r.rid]
-                    if o.footprint > self.budget:
-                        o.error = f"footprint {o.footprint} B exceeds the budget {self.budget} B"
+                    key = self.group_of(r)
+                    extra = 0 if key in groups else int(self.group_reserve(key))
+                    if o.footprint + extra > self.budget:
+                        o.error = f"footprint {o.footprint} B (+ {extra} B batch) exceeds the budget {self.budget} B"
                         pending.popleft()
                         continue
-                    if used[0] + o.footprint > self.budget:
+                    if used[0] + o.footprint + extra > self.budget:
                         break
                     pending.popleft()
                     o.slot = free_slots.pop()
                     o.admitted_s = now
                     used[0] += o.footprint
                     active[0] += 1
-                    self.peak_active = max(self.peak_active, active[0])
-                    self.peak_bytes = max(self.peak_bytes, used[0])
                     if r.steps < 1:
                         release(o)
                         continue
                     th = threading.Thread(target=opener, args=(r, o), daemon=True)
                     threads.append(th)
                     th.start()
-                    key = self.group_of(r)
                     if key not in groups:
+                        reserved[key] = extra
+                        used[0] += extra
                         g = threading.Thread(target=worker, args=(key,), daemon=True)
                         groups[key] = g
                         threads.append(g)
                         g.start()
-                if not pending and not active[0]:
+                    self.peak_active = max(self.peak_active, active[0])
+                    self.peak_bytes = max(self.peak_bytes, used[0])
+                if not pending and not active[0] and not groups:
                     break
                 timeout = 0.05
                 if pending and pending[0].arrival_s > now:
@@ -386,12 +398,48 @@ def tuned_batch_shape(workload: str, precision: str, path: str | None = None) ->
         return {"pair_tile": 0, "tiles_per_launch": 0}
 
 
+# Batching pays where one system's exchange leaves the GPU idle: workloads with fewer
+# unordered pairs per exchange than this share batches, larger ones (Si216: 93,528
+# pairs, which fill the GPU alone) run one system per group.
+BATCH_MAX_PAIRS = 50000
+# cap on a batch's pair intermediate (the launch-group size is reduced to fit)
+BATCH_X_BYTES = 4 << 30
+
+
+def _pair_tile_bytes(workload: str, precision: str) -> int:
+    import synthetic as syn
+    n = syn.si_workload(workload)["n"]
+    return 16 * int(n[0]) * int(n[1]) * int(n[2]) * (8 if precision == "mixed" else 16)
+
+
+def batch_group(req) -> object:
+    """Group key of a request: its workload when that workload is batched, else its own."""
+    import synthetic as syn
+    n = syn.si_workload(req.workload)["n_orb"]
+    return req.workload if n * (n + 1) // 2 < BATCH_MAX_PAIRS else (req.workload, req.rid)
+
+
+def batch_shape(workload: str, precision: str) -> dict:
+    """Tuned shape, with the launch-group size capped so the pair intermediate fits BATCH_X_BYTES."""
+    shape = tuned_batch_shape(workload, precision)
+    cap = max(1, BATCH_X_BYTES // _pair_tile_bytes(workload, precision))
+    tpl = shape["tiles_per_launch"]
+    shape["tiles_per_launch"] = cap if tpl == 0 else min(tpl, cap)
+    return shape
+
+
+def batch_reserve(key, precision: str = "mixed") -> int:
+    """Bytes a group's batch holds: its capped pair intermediate plus room for the tile table."""
+    workload = key if isinstance(key, str) else key[0]
+    return batch_shape(workload, precision)["tiles_per_launch"] * _pair_tile_bytes(workload, precision) + (64 << 20)
+
+
 def cuda_batch_factory():
-    """make_batch(systems) for BatchedServer: a pt_batch over the systems with the tuned shape."""
+    """make_batch(systems) for BatchedServer: a pt_batch over the systems with the tuned, capped shape."""
     from .system import Batch
 
     def make_batch(systems):
-        shape = tuned_batch_shape(systems[0].workload, systems[0].precision)
+        shape = batch_shape(systems[0].workload, systems[0].precision)
         return Batch(systems, pair_tile=shape["pair_tile"], tiles_per_launch=shape["tiles_per_launch"])
 
     return make_batch
@@ -467,7 +515,8 @@ def main(argv=None) -> None:
         srv = Server(footprint, open_system, budget, args.max_active, keep_orbitals=args.check_alone)
     else:
         srv = BatchedServer(footprint, open_system, cuda_batch_factory(), budget, args.max_active,
-                            keep_orbitals=args.check_alone)
+                            keep_orbitals=args.check_alone, group_of=batch_group,
+                            group_reserve=lambda key: batch_reserve(key, args.precision))
     outs = srv.run(reqs)
     n_orb = {k: syn.si_workload(k)["n_orb"] for k in ("si8", "si64", "si216")}
     res = summarize(outs, srv.wall_s, syn.DT_50AS, lambda wl: n_orb[wl] * (n_orb[wl] + 1) // 2)
@@ -476,8 +525,10 @@ def main(argv=None) -> None:
                 "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes,
                 "scheduling": "per-request" if args.per_request else "continuous batching",
                 **({} if args.per_request else {"peak_batch": srv.peak_batch, "ticks": srv.ticks,
-                                                "batch_shape": {w: tuned_batch_shape(w, args.precision)
-                                                                for w in sorted({r.workload for r in reqs})}})})
+                                                "batch_shape": {w: batch_shape(w, args.precision)
+                                                                for w in sorted({r.workload for r in reqs})},
+                                                "batched_workloads": sorted({r.workload for r in reqs
+                                                                             if isinstance(batch_group(r), str)})})})
     if args.check_alone:
         alone = Server(footprint, open_system, budget, 1, keep_orbitals=True)
         worst_psi, worst_e = 0.0, 0.0

@@ -91,9 +91,9 @@ def test_apply_h(pkg, mode):
     s.close()
 
 
-@pytest.mark.parametrize("fock_mode", ["exact", "ace"])
-def test_ptcn_steps_fp64(pkg, fock_mode):
-    w = dict(NONCUBIC, n_orb=6, fock_mode=fock_mode, scf_fixed_iters=4, relax_iters=3, dt=1.0)
+@pytest.mark.parametrize("fock_mode,outer", [("exact", 0), ("ace", 0), ("ace", 2)])
+def test_ptcn_steps_fp64(pkg, fock_mode, outer):
+    w = dict(NONCUBIC, n_orb=6, fock_mode=fock_mode, scf_fixed_iters=4, relax_iters=3, dt=1.0, ace_outer=outer)
     model, C0 = make(w, seed=2)
     st = model.init_state(C0)
     s = pkg.System(w, C0)

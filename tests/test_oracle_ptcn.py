@@ -89,19 +89,38 @@ def test_anderson_reaches_plain_fixed_point():
     assert np.max(np.abs(outs[0][0] - outs[1][0])) < 1e-10
 
 
-def test_step_output_orthonormal_and_ace_matches_exact():
-    res = {}
-    for mode in ("exact", "ace"):
-        p = tiny_params(fock_mode=mode, omega=0.3, scf_tol=1e-12, dt=0.5)
-        m = pc.Model(p)
-        C0 = syn.initial_coefficients(m.grid.g2_basis(), 3, seed=7)
-        st = m.init_state(C0)
+def ace_vs_exact_one_step(dt, outer):
+    """Projector and energy differences after one step: ACE (with `outer` rebuilds) vs exact."""
+    out = {}
+    for mode, k in (("exact", 0), ("ace", outer)):
+        m = pc.Model(tiny_params(fock_mode=mode, omega=0.3, scf_tol=1e-13, scf_max=400, dt=dt, ace_outer=k))
+        st = m.init_state(syn.initial_coefficients(m.grid.g2_basis(), 3, seed=7))
         st2, info = m.step(st)
+        assert info.converged
         S = st2.Psi.conj().T @ st2.Psi
         assert np.max(np.abs(S - np.eye(3))) < 1e-13
-        res[mode] = st2
-    # both modes use the same W for R_n and differ only through K_ACE inside the loop
-    assert abs(res["exact"].energy - res["ace"].energy) < 1e-2 * abs(res["exact"].energy)
+        out[mode] = st2
+    e, a = out["exact"], out["ace"]
+    dP = np.linalg.norm(e.Psi @ e.Psi.conj().T - a.Psi @ a.Psi.conj().T)
+    return dP, abs(e.energy - a.energy)
+
+
+def test_ace_once_per_step_is_second_order_per_step():
+    # Both modes share W = V_X Psi_n for R_n; inside the SCF, ACE built from Psi_n differs
+    # from V_X[Psi_f] by O(dt), which enters the step through dt/2: O(dt^2) per step.
+    d = [ace_vs_exact_one_step(dt, 0) for dt in (0.5, 0.25, 0.125)]
+    for (p1, e1), (p2, e2) in zip(d, d[1:]):
+        assert 3.5 < p1 / p2 < 4.5 and 3.5 < e1 / e2 < 4.5, d
+    assert d[0][0] < 2.5e-3 and d[0][1] < 5e-3, d
+
+
+def test_outer_ace_rebuilds_raise_the_order():
+    # a rebuild from the converged Psi_f (= Psi_{n+1} + O(dt^2)) leaves an O(dt^2) operator
+    # error: O(dt^3) per step; a second rebuild O(dt^4)
+    d1 = [ace_vs_exact_one_step(dt, 1)[0] for dt in (0.5, 0.25, 0.125)]
+    assert all(6.5 < a / b < 9.5 for a, b in zip(d1, d1[1:])), d1
+    d2 = [ace_vs_exact_one_step(dt, 2)[0] for dt in (0.5, 0.25)]
+    assert 12.0 < d2[0] / d2[1] < 20.0 and d2[0] < 1e-7, d2
 
 
 def test_cholesky_helper():

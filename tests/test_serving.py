@@ -305,3 +305,26 @@ def test_batched_results_are_the_same_alone_and_in_the_mix():
         (a,) = Server(lambda r: 1, OracleSystem, budget_bytes=3, max_active=1, keep_orbitals=True).run([r])
         assert o.error is None and a.error is None
         assert np.array_equal(a.orbitals, o.orbitals) and a.energy == o.energy
+
+
+def test_batched_server_reserves_batch_memory():
+    reset_counts()
+    # two groups; each group's batch holds 30 bytes while it runs: the si64 request must
+    # wait for the si8 group to finish (40 + 30 + 40 + 30 > 100)
+    reqs = [Request(0, "si8", 4, 0.0), Request(1, "si64", 2, 0.0)]
+    srv = BatchedServer(lambda r: 40, lambda r, s: SleepSystem(r, s), SeqBatch, budget_bytes=100, max_active=4,
+                        group_reserve=lambda key: 30)
+    outs = srv.run(reqs)
+    assert all(o.error is None for o in outs)
+    assert srv.peak_bytes <= 100
+    assert outs[1].admitted_s >= outs[0].finished_s - 1e-6
+
+
+def test_batch_policy_of_the_cuda_backend():
+    import paper_1905_01348_gb300.serve as serve
+    assert serve.batch_group(Request(0, "si8", 1)) == "si8"
+    assert serve.batch_group(Request(1, "si64", 1)) == "si64"
+    assert serve.batch_group(Request(2, "si216", 1)) == ("si216", 2)       # fills the GPU alone
+    shape = serve.batch_shape("si216", "mixed")
+    assert shape["tiles_per_launch"] * 16 * 96 ** 3 * 8 <= serve.BATCH_X_BYTES
+    assert serve.batch_reserve("si8") > 0 and serve.batch_reserve(("si216", 2)) <= serve.BATCH_X_BYTES + (64 << 20)
