@@ -193,6 +193,159 @@ __global__ void __launch_bounds__(Cfg2<L>::NT, Cfg2<L>::MINB) k_fast_f2(float2* 
   for (int e = tid; e < SLAB; e += NT) slab[e] = buf[(e / L) * W + e % L];
 }
 
+// F2 for 96-point lines with the lines in registers. Two threads share a line of
+// L = 96 = 12 x 8 points, n = n1 + 12 n2, k = k2 + 8 k1: thread half h holds the
+// points of n1 in [6h, 6h + 6) (48 values). Forward: 8-point DFTs over n2 in registers
+// (twiddle W96^(n1 k2)), then the two halves exchange by warp shuffles so that half h
+// holds k2 in [4h, 4h + 4) for all twelve n1, and 12-point DFTs over n1 give the outputs
+// k2 + 8 k1. The inverse runs the same steps backwards. Shared memory only carries the
+// slab between the row and the column passes (two transposes), rows padded to 97.
+// Column pass: for each owned k2, forward 12-point DFT, kernel multiply, inverse
+// 12-point DFT, all in registers.
+namespace l96 {
+constexpr int L = 96, W = L + 1;
+
+// 8-point DFTs over n2 of the owned n1 = 6h + a, then the twiddle W96^(n1 k2) (forward)
+__device__ __forceinline__ void stage_a_fwd(float2 (&v)[6][8], int h, const float2* tw) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    dft<8, false>(v[a]);
+    const int n1 = 6 * h + a;
+#pragma unroll
+    for (int k2 = 1; k2 < 8; ++k2) v[a][k2] = cmul(v[a][k2], tw[(n1 * k2) % L]);
+  }
+}
+
+// inverse 8-point DFTs over k2: v[a][n2] = x[6h + a + 12 n2]
+__device__ __forceinline__ void stage_a_inv(float2 (&v)[6][8]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) dft<8, true>(v[a]);
+}
+
+// forward exchange for k2 = 4h + b: z[n1], n1 = 0..11, from the owned v[.][b or 4 + b] and the partner's
+__device__ __forceinline__ void exch_fwd(const float2 (&v)[6][8], int h, int b, float2 (&z)[12]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float2 mine = h ? v[a][4 + b] : v[a][b];   // my k2 = 4h + b
+    const float2 send = h ? v[a][b] : v[a][4 + b];   // the partner's k2 = 4(1 - h) + b
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+    z[a] = h ? got : mine;        // n1 = a (owned by half 0)
+    z[6 + a] = h ? mine : got;    // n1 = 6 + a (owned by half 1)
+  }
+}
+
+// inverse twiddle of Z[n1][k2], k2 = 4h + b, then the exchange back into v[a][b], v[a][4 + b]
+__device__ __forceinline__ void exch_inv(float2 (&z)[12], int h, int b, const float2* tw, float2 (&v)[6][8]) {
+  const int k2 = 4 * h + b;
+#pragma unroll
+  for (int n1 = 1; n1 < 12; ++n1) {
+    float2 w = tw[(n1 * k2) % L];
+    w.y = -w.y;
+    z[n1] = cmul(z[n1], w);
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float2 mine = h ? z[6 + a] : z[a];          // my n1 = 6h + a
+    const float2 send = h ? z[a] : z[6 + a];          // the partner's n1
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);  // my n1, the partner's k2 = 4(1 - h) + b
+    v[a][b] = h ? got : mine;
+    v[a][4 + b] = h ? mine : got;
+  }
+}
+}  // namespace l96
+
+template <int L>
+__global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, const PairTile* __restrict__ tiles,
+                                                     int tile0, const float* __restrict__ khat_t,
+                                                     const float2* __restrict__ tw_g, int reach) {
+  static_assert(L == l96::L, "register-line F2 is written for 96-point lines");
+  using namespace l96;
+  constexpr int SLAB = L * L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* buf = tw + L;                       // [row][W]
+  const int tid = threadIdx.x, line = tid >> 1, h = tid & 1;
+  const int slot = blockIdx.y;
+  if (slot % NPAIR >= tiles[tile0 + slot / NPAIR].n_pairs) return;
+  const int i2 = (int)blockIdx.x <= reach ? (int)blockIdx.x : (int)blockIdx.x + (L - (int)gridDim.x);
+  for (int t = tid; t < L; t += 192) tw[t] = tw_g[t];
+  float2* slab = X + ((long)slot * L + i2) * SLAB;
+  float2 v[6][8];
+  // row `line` (axis 1): v[a][n2] = x[6h + a + 12 n2], two points per 16-byte load
+  {
+    const float2* row = slab + line * L + 6 * h;
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2)
+#pragma unroll
+      for (int a = 0; a < 6; a += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(row + 12 * n2 + a);
+        v[a][n2] = make_float2(q.x, q.y);
+        v[a + 1][n2] = make_float2(q.z, q.w);
+      }
+  }
+  __syncthreads();   // twiddles in place
+  // ---- forward along axis 1 (rows), outputs k = k2 + 8 k1 into buf[line][k]
+  stage_a_fwd(v, h, tw);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    float2 z[12];
+    exch_fwd(v, h, b, z);
+    dft12<false>(z);
+#pragma unroll
+    for (int k1 = 0; k1 < 12; ++k1) buf[line * W + 4 * h + b + 8 * k1] = z[k1];
+  }
+  __syncthreads();
+  // ---- axis 0 (columns): column c = line; forward, kernel multiply, inverse
+  {
+    const int c = line;
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) v[a][n2] = buf[(6 * h + a + 12 * n2) * W + c];
+    stage_a_fwd(v, h, tw);
+    const float* kt = khat_t + (long)i2 * SLAB + c;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float2 z[12];
+      exch_fwd(v, h, b, z);
+      dft12<false>(z);                                   // frequency k0 = 4h + b + 8 k1 along axis 0
+#pragma unroll
+      for (int k1 = 0; k1 < 12; ++k1) z[k1] = cscale(z[k1], __ldg(kt + (4 * h + b + 8 * k1) * L));
+      dft12<true>(z);                                    // back to n1, this k2
+      exch_inv(z, h, b, tw, v);
+    }
+    stage_a_inv(v);
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) buf[(6 * h + a + 12 * n2) * W + c] = v[a][n2];
+  }
+  __syncthreads();
+  // ---- inverse along axis 1 (rows): inputs buf[line][k2 + 8 k1], outputs to the slab
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    float2 z[12];
+#pragma unroll
+    for (int k1 = 0; k1 < 12; ++k1) z[k1] = buf[line * W + 4 * h + b + 8 * k1];
+    dft12<true>(z);
+    exch_inv(z, h, b, tw, v);
+  }
+  stage_a_inv(v);
+  {
+    float2* row = slab + line * L + 6 * h;
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2)
+#pragma unroll
+      for (int a = 0; a < 6; a += 2)
+        *reinterpret_cast<float4*>(row + 12 * n2 + a) = make_float4(v[a][n2].x, v[a][n2].y, v[a + 1][n2].x,
+                                                                    v[a + 1][n2].y);
+  }
+}
+
 // F3: inverse FFT along axis 2 for all pairs of the tile, then each output
 // orbital adds its listed contributions to its W rows (one writer per row).
 // The live slabs of X arrive by asynchronous copies straight into shared
@@ -294,6 +447,10 @@ static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* 
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f2<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
     if (e != cudaSuccess) return e;
+    if constexpr (L == 96) {
+      e = cudaFuncSetAttribute(k_fast_f2r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
+      if (e != cudaSuccess) return e;
+    }
     attr_done.fetch_or(bit, std::memory_order_release);
   }
   float2* X = (float2*)scratch;
@@ -304,7 +461,8 @@ static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* 
     dim3 g13((unsigned)(L * (L / RR)), (unsigned)nt);
     k_fast_f1<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     dim3 g2((unsigned)n_live, (unsigned)(nt * NPAIR));
-    k_fast_f2<L><<<g2, Cfg2<L>::NT, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
+    if constexpr (L == 96) k_fast_f2r<L><<<g2, 192, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
+    else k_fast_f2<L><<<g2, Cfg2<L>::NT, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
     k_fast_f3<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     launched(3);
   }

@@ -297,28 +297,32 @@ class BatchedServer:
                             release(o)
                     running, batch, members = [], None, ()
                     continue
-                with cv:
-                    self.ticks += 1
-                    self.peak_batch = max(self.peak_batch, len(running))
-                    keep = []
-                    for x, info in zip(running, infos):
-                        req, o, system, k = x
-                        o.step_ms.append(dt_ms)
-                        o.energy.append(info["energy"])
-                        o.dipole.append(list(info["dipole"]))
-                        o.scf_iters.append(info["scf_iters"])
-                        x[3] = k + 1
-                        if x[3] >= req.steps:
-                            if self.keep_orbitals:
-                                o.orbitals = system.orbitals()
-                            close_quietly(o, system)
-                            release(o)
-                        else:
-                            keep.append(x)
-                    running = keep
-                if not running and batch is not None:
+                keep, done = [], []
+                for x, info in zip(running, infos):
+                    x[1].step_ms.append(dt_ms)
+                    x[1].energy.append(info["energy"])
+                    x[1].dipole.append(list(info["dipole"]))
+                    x[1].scf_iters.append(info["scf_iters"])
+                    x[3] += 1
+                    (done if x[3] >= x[0].steps else keep).append(x)
+                running = keep
+                finished = []
+                if done:
+                    # the batch refers to the finished systems: close it first, so that their
+                    # device memory is free before their budget is returned
                     batch.close()
                     batch, members = None, ()
+                    for req, o, system, _ in done:
+                        if self.keep_orbitals:
+                            o.orbitals = system.orbitals()
+                        close_quietly(o, system)
+                        finished.append(o)
+                    done = []
+                with cv:
+                    self.ticks += 1
+                    self.peak_batch = max(self.peak_batch, len(infos))
+                    for o in finished:
+                        release(o)
 
         with cv:
             while pending or active[0] or groups:

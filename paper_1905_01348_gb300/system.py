@@ -83,9 +83,12 @@ class System:
         return nat.pt_propagate(self.handle, nsteps)
 
     def close(self) -> None:
+        """Destroy the handle and release the workspace (its memory returns to the allocator
+        now, even while other objects still refer to this System)."""
         if getattr(self, "handle", None) is not None:
             nat.pt_destroy(self.handle)
             self.handle = None
+        self.workspace = None
 
     def __del__(self):
         try:
@@ -129,6 +132,8 @@ class Batch:
         if getattr(self, "handle", None) is not None:
             nat.pt_batch_destroy(self.handle)
             self.handle = None
+        self.workspace = None
+        self.systems = []
 
     def __del__(self):
         try:
