@@ -133,6 +133,69 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const PairTile* __r
   }
 }
 
+// Register-line transforms of 96-point lines (L = 96 = 12 x 8, n = n1 + 12 n2,
+// k = k2 + 8 k1): two threads share a line, thread half h holding n1 in [6h, 6h + 6)
+// (48 values); the partner is the lane XM apart. Used by F2 at 96^3.
+namespace l96 {
+constexpr int L = 96, W = L + 1;
+
+// Twiddle indices n1 k2 stay below 96 (n1 < 12, k2 < 8), so they need no reduction.
+
+// 8-point DFTs over n2 of the owned n1 = 6h + a, then the twiddle W96^(n1 k2) (forward)
+__device__ __forceinline__ void stage_a_fwd(float2 (&v)[6][8], int h, const float2* tw) {
+  const int h6 = 6 * h;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    dft<8, false>(v[a]);
+#pragma unroll
+    for (int k2 = 1; k2 < 8; ++k2) v[a][k2] = cmul(v[a][k2], tw[a * k2 + h6 * k2]);
+  }
+}
+
+// inverse 8-point DFTs over k2: v[a][n2] = x[6h + a + 12 n2]
+__device__ __forceinline__ void stage_a_inv(float2 (&v)[6][8]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) dft<8, true>(v[a]);
+}
+
+// forward exchange for k2 = 4h + b: z[n1], n1 = 0..11, from the owned v[.][b or 4 + b] and the partner's
+template <int XM = 1>
+__device__ __forceinline__ void exch_fwd(const float2 (&v)[6][8], int h, int b, float2 (&z)[12]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float2 mine = h ? v[a][4 + b] : v[a][b];   // my k2 = 4h + b
+    const float2 send = h ? v[a][b] : v[a][4 + b];   // the partner's k2 = 4(1 - h) + b
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, XM);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, XM);
+    z[a] = h ? got : mine;        // n1 = a (owned by half 0)
+    z[6 + a] = h ? mine : got;    // n1 = 6 + a (owned by half 1)
+  }
+}
+
+// inverse twiddle of Z[n1][k2], k2 = 4h + b, then the exchange back into v[a][b], v[a][4 + b]
+template <int XM = 1>
+__device__ __forceinline__ void exch_inv(float2 (&z)[12], int h, int b, const float2* tw, float2 (&v)[6][8]) {
+  const int h4 = 4 * h;
+#pragma unroll
+  for (int n1 = 1; n1 < 12; ++n1) {
+    float2 w = tw[n1 * b + n1 * h4];
+    w.y = -w.y;
+    z[n1] = cmul(z[n1], w);
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float2 mine = h ? z[6 + a] : z[a];          // my n1 = 6h + a
+    const float2 send = h ? z[a] : z[6 + a];          // the partner's n1
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, XM);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, XM);  // my n1, the partner's k2 = 4(1 - h) + b
+    v[a][b] = h ? got : mine;
+    v[a][4 + b] = h ? mine : got;
+  }
+}
+}  // namespace l96
+
 // F2: one live (pair, i2) slab per block: asynchronous copies into the padded
 // work buffer, FFT along axis 1 and axis 0, multiply by the screened kernel
 // (fused between the last forward and first inverse stage of axis 0), inverse
@@ -198,65 +261,11 @@ __global__ void __launch_bounds__(Cfg2<L>::NT, Cfg2<L>::MINB) k_fast_f2(float2* 
 // points of n1 in [6h, 6h + 6) (48 values). Forward: 8-point DFTs over n2 in registers
 // (twiddle W96^(n1 k2)), then the two halves exchange by warp shuffles so that half h
 // holds k2 in [4h, 4h + 4) for all twelve n1, and 12-point DFTs over n1 give the outputs
-// k2 + 8 k1. The inverse runs the same steps backwards. Shared memory only carries the
-// slab between the row and the column passes (two transposes), rows padded to 97.
-// Column pass: for each owned k2, forward 12-point DFT, kernel multiply, inverse
-// 12-point DFT, all in registers.
-namespace l96 {
-constexpr int L = 96, W = L + 1;
-
-// 8-point DFTs over n2 of the owned n1 = 6h + a, then the twiddle W96^(n1 k2) (forward)
-__device__ __forceinline__ void stage_a_fwd(float2 (&v)[6][8], int h, const float2* tw) {
-#pragma unroll
-  for (int a = 0; a < 6; ++a) {
-    dft<8, false>(v[a]);
-    const int n1 = 6 * h + a;
-#pragma unroll
-    for (int k2 = 1; k2 < 8; ++k2) v[a][k2] = cmul(v[a][k2], tw[(n1 * k2) % L]);
-  }
-}
-
-// inverse 8-point DFTs over k2: v[a][n2] = x[6h + a + 12 n2]
-__device__ __forceinline__ void stage_a_inv(float2 (&v)[6][8]) {
-#pragma unroll
-  for (int a = 0; a < 6; ++a) dft<8, true>(v[a]);
-}
-
-// forward exchange for k2 = 4h + b: z[n1], n1 = 0..11, from the owned v[.][b or 4 + b] and the partner's
-__device__ __forceinline__ void exch_fwd(const float2 (&v)[6][8], int h, int b, float2 (&z)[12]) {
-#pragma unroll
-  for (int a = 0; a < 6; ++a) {
-    const float2 mine = h ? v[a][4 + b] : v[a][b];   // my k2 = 4h + b
-    const float2 send = h ? v[a][b] : v[a][4 + b];   // the partner's k2 = 4(1 - h) + b
-    float2 got;
-    got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-    got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
-    z[a] = h ? got : mine;        // n1 = a (owned by half 0)
-    z[6 + a] = h ? mine : got;    // n1 = 6 + a (owned by half 1)
-  }
-}
-
-// inverse twiddle of Z[n1][k2], k2 = 4h + b, then the exchange back into v[a][b], v[a][4 + b]
-__device__ __forceinline__ void exch_inv(float2 (&z)[12], int h, int b, const float2* tw, float2 (&v)[6][8]) {
-  const int k2 = 4 * h + b;
-#pragma unroll
-  for (int n1 = 1; n1 < 12; ++n1) {
-    float2 w = tw[(n1 * k2) % L];
-    w.y = -w.y;
-    z[n1] = cmul(z[n1], w);
-  }
-#pragma unroll
-  for (int a = 0; a < 6; ++a) {
-    const float2 mine = h ? z[6 + a] : z[a];          // my n1 = 6h + a
-    const float2 send = h ? z[a] : z[6 + a];          // the partner's n1
-    float2 got;
-    got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-    got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);  // my n1, the partner's k2 = 4(1 - h) + b
-    v[a][b] = h ? got : mine;
-    v[a][4 + b] = h ? mine : got;
-  }
-}
-}  // namespace l96
+// k2 + 8 k1. The inverse runs the same steps backwards. The slab arrives by cp.async
+// into a shared buffer (rows padded to 97) and leaves from it; between the passes the
+// lines cross shared memory once per pass instead of once per radix stage. Column
+// pass: for each owned k2, forward 12-point DFT, kernel multiply, inverse 12-point DFT,
+// all in registers.
 
 template <int L>
 __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, const PairTile* __restrict__ tiles,
@@ -265,41 +274,41 @@ __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, con
   static_assert(L == l96::L, "register-line F2 is written for 96-point lines");
   using namespace l96;
   constexpr int SLAB = L * L;
+  constexpr int XM = 16;                      // the two halves of a line are the lanes 16 apart
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* buf = tw + L;                       // [row][W]
-  const int tid = threadIdx.x, line = tid >> 1, h = tid & 1;
+  const int tid = threadIdx.x, lane = tid & 31;
+  // a half-warp holds the same half h of 16 consecutive lines: its shared-memory accesses
+  // (one row of 16 lines, or 16 columns of one row) fall on distinct banks
+  const int line = (tid >> 5) * 16 + (lane & 15), h = lane >> 4;
   const int slot = blockIdx.y;
   if (slot % NPAIR >= tiles[tile0 + slot / NPAIR].n_pairs) return;
   const int i2 = (int)blockIdx.x <= reach ? (int)blockIdx.x : (int)blockIdx.x + (L - (int)gridDim.x);
   for (int t = tid; t < L; t += 192) tw[t] = tw_g[t];
   float2* slab = X + ((long)slot * L + i2) * SLAB;
+  for (int e = tid; e < SLAB; e += 192) cp_async8(buf + (e / L) * W + e % L, slab + e);
+  cp_async_wait_all();
+  __syncthreads();
   float2 v[6][8];
-  // row `line` (axis 1): v[a][n2] = x[6h + a + 12 n2], two points per 16-byte load
-  {
-    const float2* row = slab + line * L + 6 * h;
+  // ---- forward along axis 1 (rows): v[a][n2] = x[6h + a + 12 n2] of row `line`; outputs
+  // k = k2 + 8 k1 back into the row
 #pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2)
+  for (int n2 = 0; n2 < 8; ++n2)
 #pragma unroll
-      for (int a = 0; a < 6; a += 2) {
-        const float4 q = *reinterpret_cast<const float4*>(row + 12 * n2 + a);
-        v[a][n2] = make_float2(q.x, q.y);
-        v[a + 1][n2] = make_float2(q.z, q.w);
-      }
-  }
-  __syncthreads();   // twiddles in place
-  // ---- forward along axis 1 (rows), outputs k = k2 + 8 k1 into buf[line][k]
+    for (int a = 0; a < 6; ++a) v[a][n2] = buf[line * W + 6 * h + a + 12 * n2];
+  __syncthreads();   // every row is in registers before any is overwritten
   stage_a_fwd(v, h, tw);
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     float2 z[12];
-    exch_fwd(v, h, b, z);
+    exch_fwd<XM>(v, h, b, z);
     dft12<false>(z);
 #pragma unroll
     for (int k1 = 0; k1 < 12; ++k1) buf[line * W + 4 * h + b + 8 * k1] = z[k1];
   }
   __syncthreads();
-  // ---- axis 0 (columns): column c = line; forward, kernel multiply, inverse
+  // ---- axis 0 (columns): column c = line; forward, kernel multiply, inverse, in registers
   {
     const int c = line;
 #pragma unroll
@@ -311,12 +320,12 @@ __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, con
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       float2 z[12];
-      exch_fwd(v, h, b, z);
+      exch_fwd<XM>(v, h, b, z);
       dft12<false>(z);                                   // frequency k0 = 4h + b + 8 k1 along axis 0
 #pragma unroll
       for (int k1 = 0; k1 < 12; ++k1) z[k1] = cscale(z[k1], __ldg(kt + (4 * h + b + 8 * k1) * L));
       dft12<true>(z);                                    // back to n1, this k2
-      exch_inv(z, h, b, tw, v);
+      exch_inv<XM>(z, h, b, tw, v);
     }
     stage_a_inv(v);
 #pragma unroll
@@ -325,25 +334,23 @@ __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, con
       for (int a = 0; a < 6; ++a) buf[(6 * h + a + 12 * n2) * W + c] = v[a][n2];
   }
   __syncthreads();
-  // ---- inverse along axis 1 (rows): inputs buf[line][k2 + 8 k1], outputs to the slab
+  // ---- inverse along axis 1 (rows): inputs k2 + 8 k1 of row `line`, outputs back into it
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     float2 z[12];
 #pragma unroll
     for (int k1 = 0; k1 < 12; ++k1) z[k1] = buf[line * W + 4 * h + b + 8 * k1];
     dft12<true>(z);
-    exch_inv(z, h, b, tw, v);
+    exch_inv<XM>(z, h, b, tw, v);
   }
   stage_a_inv(v);
-  {
-    float2* row = slab + line * L + 6 * h;
+  __syncthreads();   // every row is in registers before any is overwritten
 #pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2)
+  for (int n2 = 0; n2 < 8; ++n2)
 #pragma unroll
-      for (int a = 0; a < 6; a += 2)
-        *reinterpret_cast<float4*>(row + 12 * n2 + a) = make_float4(v[a][n2].x, v[a][n2].y, v[a + 1][n2].x,
-                                                                    v[a + 1][n2].y);
-  }
+    for (int a = 0; a < 6; ++a) buf[line * W + 6 * h + a + 12 * n2] = v[a][n2];
+  __syncthreads();
+  for (int e = tid; e < SLAB; e += 192) slab[e] = buf[(e / L) * W + e % L];
 }
 
 // F3: inverse FFT along axis 2 for all pairs of the tile, then each output

@@ -382,6 +382,11 @@ def summarize(outcomes, wall_s: float, dt_au: float, pairs_of) -> dict:
         "errors": {o.rid: o.error for o in outcomes if o.error},
         "steps": n_steps, "wall_s": wall_s,
         "step_latency_ms": {"p50": percentile(steps, 0.50), "p99": percentile(steps, 0.99)},
+        "step_latency_ms_by_workload": {
+            wl: {"p50": percentile([ms for o in outcomes if o.workload == wl for ms in o.step_ms], 0.50),
+                 "p99": percentile([ms for o in outcomes if o.workload == wl for ms in o.step_ms], 0.99),
+                 "steps": sum(len(o.step_ms) for o in outcomes if o.workload == wl)}
+            for wl in sorted({o.workload for o in outcomes})},
         "queue_wait_s": {"p50": percentile(waits, 0.50), "p99": percentile(waits, 0.99)},
         "fs_per_day": fs / wall_s * 86400.0 if wall_s > 0 else None,
         "pair_solves_per_s": pairs / wall_s if wall_s > 0 else None,
