@@ -247,7 +247,7 @@ static pt_status ensure_plan_x(pt_system* sys, int ncols) {
   sys->plan_x.launch_count = lc;
   sys->plan_x.d_tiles = sys->d_tiles_x;
   sys->plan_x.n_tiles = nt;
-  sys->plan_x.g2_reach = pair_g2_reach(&sys->p);
+  set_pair_reach(&sys->plan_x, &sys->p);
   sys->plan_x_ncols = ncols;
   return PT_OK;
 }

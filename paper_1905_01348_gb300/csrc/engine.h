@@ -144,7 +144,7 @@ int freq(int i, int n);   // FFT index -> signed frequency
 void basis_list(const pt_params* p, std::vector<int>* idx, std::vector<double>* g2out);
 pt_params fock_params(const pt_params* p);   // the parameters with the Fock grid as the grid
 bool fock_is_own(const pt_params* p);
-int pair_g2_reach(const pt_params* p);
+void set_pair_reach(pt::FockPlan* plan, const pt_params* p);
 int choose_tile(const pt_params* p);
 int tiles_per_launch(const pt_params* p, long N, bool mixed);
 int h_batch(const pt_params* p);

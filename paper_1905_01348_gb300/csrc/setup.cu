@@ -77,13 +77,26 @@ static long fock_points(const pt_params* p) {
   return (long)q.n[0] * q.n[1] * q.n[2];
 }
 
-// Twice the largest |g2| over the basis: the reach of pair products along axis 2.
-int pair_g2_reach(const pt_params* p) {
+// The reach of pair products (Eq. 3: products of two basis-limited orbitals): twice the
+// largest |g1| and |g2| index of the basis along axes 1 and 2, and the ball of twice the
+// largest |G| (|G_a - G_b| <= |G_a| + |G_b|).
+void set_pair_reach(pt::FockPlan* plan, const pt_params* p) {
   std::vector<int> idx;
-  basis_list(p, &idx, nullptr);
-  int m = 0;
-  for (int v : idx) m = std::max(m, std::abs(freq(v % p->n[2], p->n[2])));
-  return 2 * m;
+  std::vector<double> g2;
+  basis_list(p, &idx, &g2);
+  int m1 = 0, m2 = 0;
+  double gmax2 = 0.0;
+  for (size_t k = 0; k < idx.size(); ++k) {
+    const int v = idx[k];
+    m2 = std::max(m2, std::abs(freq(v % p->n[2], p->n[2])));
+    m1 = std::max(m1, std::abs(freq((v / p->n[2]) % p->n[1], p->n[1])));
+    gmax2 = std::max(gmax2, g2[k]);
+  }
+  plan->g2_reach = 2 * m2;
+  plan->g1_reach = 2 * m1;
+  plan->ball_r2 = (float)(4.0 * gmax2);
+  plan->ball_dg1 = (float)(2.0 * M_PI / p->cell[1]);
+  plan->ball_dg2 = (float)(2.0 * M_PI / p->cell[2]);
 }
 
 // Screened kernel K(G) = 4 pi (1 - exp(-G^2 / (4 w^2))) / G^2, K(0) = pi / w^2 (its limit),
@@ -363,7 +376,7 @@ pt_status init_body(pt_system* sys, const double* psi0_host) {
     sys->plan_sym.launch_count = lc;
     sys->plan_sym.d_tiles = sys->d_tiles_sym;
     sys->plan_sym.n_tiles = nt;
-    sys->plan_sym.g2_reach = pair_g2_reach(p);
+    set_pair_reach(&sys->plan_sym, p);
   }
   PT_CK(cudaMemsetAsync(sys->status, 0, sizeof(int) * 16, s));
   PT_CK(cudaStreamSynchronize(s));
@@ -461,7 +474,7 @@ pt_status exchange_static_body(pt_system* t, const pt_params* p, const std::vect
   t->plan_sym.launch_count = lc;
   t->plan_sym.n_tiles = nt;
   t->plan_sym.d_tiles = t->d_tiles_sym;
-  t->plan_sym.g2_reach = pair_g2_reach(p);
+  set_pair_reach(&t->plan_sym, p);
   PT_CK(cudaMemsetAsync(t->status, 0, sizeof(int) * 16, s));
   cudaError_t e = cudaMemcpyAsync(t->d_tiles_sym, tiles, sizeof(pt::PairTile) * nt, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

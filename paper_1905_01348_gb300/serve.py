@@ -421,11 +421,25 @@ def _pair_tile_bytes(workload: str, precision: str) -> int:
     return 16 * int(n[0]) * int(n[1]) * int(n[2]) * (8 if precision == "mixed" else 16)
 
 
+def _small(workload: str) -> bool:
+    import synthetic as syn
+    n = syn.si_workload(workload)["n_orb"]
+    return n * (n + 1) // 2 < BATCH_MAX_PAIRS
+
+
 def batch_group(req) -> object:
     """Group key of a request: its workload when that workload is batched, else its own."""
-    import synthetic as syn
-    n = syn.si_workload(req.workload)["n_orb"]
-    return req.workload if n * (n + 1) // 2 < BATCH_MAX_PAIRS else (req.workload, req.rid)
+    return req.workload if _small(req.workload) else (req.workload, req.rid)
+
+
+def stream_priority(workload: str) -> int:
+    """CUDA stream priority of a workload's systems and batches: -1 (high) for the small
+    workloads, 0 for those whose exchange fills the GPU. The device dispatches the
+    blocks of queued high-priority kernels before those of queued normal ones (running
+    blocks finish), so a small request's dependent kernels do not wait behind the whole
+    queued step of a large one (measured without priorities: Si8 steps p50 0.6 s, p99
+    65 s beside Si216)."""
+    return -1 if _small(workload) else 0
 
 
 def batch_shape(workload: str, precision: str) -> dict:
@@ -449,14 +463,16 @@ def cuda_batch_factory():
 
     def make_batch(systems):
         shape = batch_shape(systems[0].workload, systems[0].precision)
-        return Batch(systems, pair_tile=shape["pair_tile"], tiles_per_launch=shape["tiles_per_launch"])
+        return Batch(systems, pair_tile=shape["pair_tile"], tiles_per_launch=shape["tiles_per_launch"],
+                     priority=stream_priority(systems[0].workload))
 
     return make_batch
 
 
 def cuda_backend(device: str = "cuda:0", max_active: int = 8):
-    """(footprint, open_system) for the CUDA library: one torch stream per slot, the
-    workspace allocated on that stream, start orbitals from the seeded generator."""
+    """(footprint, open_system) for the CUDA library: one torch stream per slot and priority
+    (stream_priority of the request's workload), the workspace allocated on that stream,
+    start orbitals from the seeded generator."""
     import torch
     import synthetic as syn
     from . import _native as nat
@@ -464,7 +480,7 @@ def cuda_backend(device: str = "cuda:0", max_active: int = 8):
 
     nat.load()
     dev = torch.device(device)
-    streams = [torch.cuda.Stream(dev) for _ in range(max_active)]
+    streams = {pr: [torch.cuda.Stream(dev, priority=pr) for _ in range(max_active)] for pr in (-1, 0)}
 
     def workload(req):
         return syn.si_workload(req.workload, precision=req.precision, fock_mode="ace", kick=tuple(req.kick))
@@ -478,8 +494,9 @@ def cuda_backend(device: str = "cuda:0", max_active: int = 8):
         p = nat.make_params(w)
         g2 = syn.basis_g2(nat.pt_basis_indices(p), w["n"], w["cell"])
         c0 = syn.initial_coefficients(g2, w["n_orb"], seed=req.seed)
-        with torch.cuda.stream(streams[slot]):
-            system = System(w, c0, device=str(dev), stream=streams[slot])
+        stream = streams[stream_priority(req.workload)][slot]
+        with torch.cuda.stream(stream):
+            system = System(w, c0, device=str(dev), stream=stream)
         system.workload, system.precision = req.workload, req.precision
         return system
 

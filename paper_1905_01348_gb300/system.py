@@ -103,10 +103,11 @@ class Batch:
     systems: System objects with the same grid, precision, cell, cutoff and kernel; each
     keeps its own stream. The batch workspace and the stream of the merged pair kernels
     come from PyTorch. pair_tile / tiles_per_launch: the tile edge and launch-group size
-    (0: automatic; the autotuner's table gives tuned values).
+    (0: automatic; the autotuner's table gives tuned values). priority: CUDA priority of
+    the batch's stream (0 normal, negative higher).
     """
 
-    def __init__(self, systems, pair_tile: int = 0, tiles_per_launch: int = 0):
+    def __init__(self, systems, pair_tile: int = 0, tiles_per_launch: int = 0, priority: int = 0):
         import torch
         self.torch = torch
         self.systems = list(systems)
@@ -114,7 +115,7 @@ class Batch:
         handles = [s.handle for s in self.systems]
         self.ws_bytes = nat.pt_batch_workspace_size(handles, pair_tile, tiles_per_launch)
         self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
-        self.stream = torch.cuda.Stream(dev)
+        self.stream = torch.cuda.Stream(dev, priority=priority)
         self.handle = nat.pt_batch_create(handles, pair_tile, tiles_per_launch, self.workspace.data_ptr(),
                                           self.ws_bytes, self.stream.cuda_stream)
 

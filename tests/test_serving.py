@@ -181,8 +181,9 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
         b.build()
 
     class FakeStream:
-        def __init__(self, device=None):
+        def __init__(self, device=None, priority=0):
             self.cuda_stream = 0
+            self.priority = priority
 
     made = []
 
@@ -190,7 +191,7 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
         def __init__(self, params, psi0, device="cuda:0", stream=None):
             assert isinstance(stream, FakeStream) and device == "cuda:0"
             assert psi0.shape[0] == params["n_orb"]
-            self.params, self.psi0, self.k = params, psi0, 0
+            self.params, self.psi0, self.k, self.stream = params, psi0, 0, stream
             made.append(self)
 
         def step(self):
@@ -203,9 +204,12 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
         def close(self):
             pass
 
+    batches = []
+
     class FakeBatch:
-        def __init__(self, systems, pair_tile=0, tiles_per_launch=0):
-            self.systems = systems
+        def __init__(self, systems, pair_tile=0, tiles_per_launch=0, priority=0):
+            self.systems, self.priority = systems, priority
+            batches.append(self)
 
         def step(self):
             return 0, [x.step()[1] for x in self.systems]
@@ -229,6 +233,9 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     assert sorted(tuple(s.params["kick"]) for s in firsts) == sorted(tuple(k) for k in kicks)
     assert sum(s.params["n_orb"] == 16 for s in firsts) == 12
     assert all(s.params["precision"] == "mixed" and s.params["fock_mode"] == "ace" for s in firsts)
+    # the small workloads (batched) run on high-priority streams, their batches too
+    assert all(s.stream.priority == -1 for s in firsts)
+    assert batches and all(bt.priority == -1 for bt in batches)
 
     assert res["scheduling"] == "continuous batching" and res["peak_batch"] >= 2
 
@@ -325,6 +332,8 @@ def test_batch_policy_of_the_cuda_backend():
     assert serve.batch_group(Request(0, "si8", 1)) == "si8"
     assert serve.batch_group(Request(1, "si64", 1)) == "si64"
     assert serve.batch_group(Request(2, "si216", 1)) == ("si216", 2)       # fills the GPU alone
+    assert serve.stream_priority("si8") == serve.stream_priority("si64") == -1
+    assert serve.stream_priority("si216") == 0
     shape = serve.batch_shape("si216", "mixed")
     assert shape["tiles_per_launch"] * 16 * 96 ** 3 * 8 <= serve.BATCH_X_BYTES
     assert serve.batch_reserve("si8") > 0 and serve.batch_reserve(("si216", 2)) <= serve.BATCH_X_BYTES + (64 << 20)
