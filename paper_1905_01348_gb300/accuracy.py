@@ -18,7 +18,14 @@ density change of 1e-8). The start
 state (orthonormalisation and relaxation) is computed by each run itself.
 Prints one JSON object.
 
+`--ace-vs-exact` instead measures the error of building ACE once per step (the
+bench's setting) against the paper's exchange, V_X applied exactly at every SCF
+iteration (Alg. 1): FP64 runs at the tight tolerance with exact exchange, with ACE
+once per step and with `ace_outer` = 1 and 2 outer rebuilds, and the mixed ACE run at
+the workload's tolerance, each compared with the exact run.
+
     python -m paper_1905_01348_gb300.accuracy --workload si8 --steps 20
+    python -m paper_1905_01348_gb300.accuracy --workload si8 --steps 20 --ace-vs-exact
 """
 from __future__ import annotations
 
@@ -40,6 +47,8 @@ def main(argv=None) -> None:
                     help="scf_fp64_below of the mixed tight run (default: the workload's)")
     ap.add_argument("--fock-grid", type=int, default=0,
                     help="also run mixed precision with the pair FFTs on this cubic grid and report the aliasing error")
+    ap.add_argument("--ace-vs-exact", action="store_true",
+                    help="compare ACE once per step (and with outer rebuilds) with exact exchange every SCF iteration")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -54,14 +63,33 @@ def main(argv=None) -> None:
     g2 = syn.basis_g2(nat.pt_basis_indices(p), base["n"], base["cell"])
     C0 = syn.initial_coefficients(g2, base["n_orb"], seed=args.seed)
     runs = {}
-    cases = [("fp64", "fp64", base["scf_tol"], None), ("mixed", "mixed", base["scf_tol"], None),
+    if args.ace_vs_exact:
+        cases = [("exact", "fp64", args.tight_tol, "exact", 0), ("ace", "fp64", args.tight_tol, "ace", 0),
+                 ("ace_outer1", "fp64", args.tight_tol, "ace", 1), ("ace_outer2", "fp64", args.tight_tol, "ace", 2),
+                 ("mixed_ace", "mixed", base["scf_tol"], "ace", 0)]
+        for name, prec, tol, mode, outer in cases:
+            s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200, fock_mode=mode, ace_outer=outer), C0)
+            e0, d0 = s.observables()
+            rec = {"energy": [e0], "dipole": [np.asarray(d0)], "scf": [], "ms": []}
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                st, info = s.step()
+                rec["ms"].append((time.perf_counter() - t0) * 1e3)
+                rec["energy"].append(info["energy"])
+                rec["dipole"].append(np.asarray(info["dipole"]))
+                rec["scf"].append(info["scf_iters"])
+            rec["psi"] = s.orbitals()
+            s.close()
+            runs[name] = rec
+    else:
+        cases = [("fp64", "fp64", base["scf_tol"], None), ("mixed", "mixed", base["scf_tol"], None),
              ("fp64_tight", "fp64", args.tight_tol, None)]
     if args.mixed_tight_tol > 0:
         cases.append(("mixed_tight", "mixed", args.mixed_tight_tol, None))
     refine = base["scf_fp64_below"] if args.refine_below is None else args.refine_below
     if args.fock_grid:
         cases.append(("mixed_fock", "mixed", base["scf_tol"], (args.fock_grid,) * 3))
-    for name, prec, tol, fock in cases:
+    for name, prec, tol, fock in ([] if args.ace_vs_exact else cases):
         s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200, fock_grid=fock,
                         scf_fp64_below=refine if name == "mixed_tight" else base["scf_fp64_below"]), C0)
         e0, d0 = s.observables()
@@ -85,6 +113,15 @@ def main(argv=None) -> None:
                 "subspace_defect": float(base["n_orb"] - np.sum(np.abs(ov) ** 2)),
                 "per_step_energy_diff": de, "per_step_dipole_diff": dd}
 
+    if args.ace_vs_exact:
+        ref = runs["exact"]
+        out = {"workload": args.workload, "steps": args.steps, "tight_tol": args.tight_tol, "scf_tol": base["scf_tol"],
+               "dt_au": base["dt"],
+               **{f"{k}_vs_exact": compare(runs[k], ref) for k in ("ace", "ace_outer1", "ace_outer2", "mixed_ace")},
+               "scf_iters": {k: r["scf"] for k, r in runs.items()},
+               "ms_per_step": {k: float(np.median(r["ms"])) for k, r in runs.items()}}
+        print(json.dumps(out))
+        return
     ref = runs["fp64_tight"]
     out = {"workload": args.workload, "steps": args.steps, "fock_mode": args.fock_mode,
            "scf_tol": base["scf_tol"], "tight_tol": args.tight_tol,

@@ -390,6 +390,17 @@ def summarize(outcomes, wall_s: float, dt_au: float, pairs_of) -> dict:
         "queue_wait_s": {"p50": percentile(waits, 0.50), "p99": percentile(waits, 0.99)},
         "fs_per_day": fs / wall_s * 86400.0 if wall_s > 0 else None,
         "pair_solves_per_s": pairs / wall_s if wall_s > 0 else None,
+        # one line per request: arrival, admission and finish (s after the start), its
+        # slowest step (index, ms) and SCF iterations (median, max)
+        "per_request": [
+            {"rid": o.rid, "workload": o.workload, "steps": len(o.step_ms), "arrival_s": round(o.arrival_s, 3),
+             "admitted_s": None if o.admitted_s is None else round(o.admitted_s, 3),
+             "finished_s": None if o.finished_s is None else round(o.finished_s, 3),
+             "slowest_step": (None if not o.step_ms else
+                              [int(max(range(len(o.step_ms)), key=o.step_ms.__getitem__)), round(max(o.step_ms), 1)]),
+             "p50_step_ms": None if not o.step_ms else round(percentile(o.step_ms, 0.5), 1),
+             "scf_iters": None if not o.scf_iters else [percentile(o.scf_iters, 0.5), max(o.scf_iters)]}
+            for o in sorted(outcomes, key=lambda o: o.rid)],
     }
 
 
