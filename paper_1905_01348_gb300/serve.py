@@ -72,11 +72,79 @@ class Outcome:
     finished_s: float | None = None
     slot: int | None = None
     step_ms: list = dataclasses.field(default_factory=list)
+    step_start_s: list = dataclasses.field(default_factory=list)   # seconds after the start of the run
     energy: list = dataclasses.field(default_factory=list)
     dipole: list = dataclasses.field(default_factory=list)
     scf_iters: list = dataclasses.field(default_factory=list)
     orbitals: object = None
     error: str | None = None
+
+
+class DeviceArena:
+    """One device buffer from which the server carves every workspace, so that nothing is
+    allocated or freed on the device while requests run. (Through PyTorch's caching
+    allocator a finished request's block stays cached for its own stream; a new request on
+    another stream then misses it, and near the budget the allocator frees its whole cache,
+    whose frees synchronise the device and hold every other thread meanwhile.)
+
+    Offsets are 256-byte aligned. Blocks of at least `large` bytes are placed at the
+    highest-addressed free range that fits, smaller ones at the lowest (first fit from
+    each end keeps the large, equal-sized workspaces from being split by small ones);
+    released ranges coalesce with their neighbours. `nbytes` with device=None keeps the
+    bookkeeping only (host tests)."""
+
+    ALIGN = 256
+
+    def __init__(self, nbytes: int, device=None, large: int = 1 << 30):
+        self.size = int(nbytes) // self.ALIGN * self.ALIGN
+        self.large = int(large)
+        self.free_ranges = [(0, self.size)] if self.size > 0 else []   # sorted by offset
+        self.used = {}                                                  # offset -> length
+        self.lock = threading.Lock()
+        self.buf = None
+        if device is not None and self.size > 0:
+            import torch
+            self.buf = torch.empty(self.size, dtype=torch.uint8, device=device)
+
+    def alloc(self, nbytes: int) -> int | None:
+        """Offset of a block of at least nbytes, or None when no free range fits."""
+        n = max(self.ALIGN, -(-int(nbytes) // self.ALIGN) * self.ALIGN)
+        with self.lock:
+            order = range(len(self.free_ranges))
+            if n >= self.large:
+                order = reversed(order)
+            for i in order:
+                off, length = self.free_ranges[i]
+                if length < n:
+                    continue
+                at = off + length - n if n >= self.large else off
+                rest = [(off, at - off)] if at > off else []
+                if at + n < off + length:
+                    rest.append((at + n, off + length - at - n))
+                self.free_ranges[i:i + 1] = rest
+                self.used[at] = n
+                return at
+            return None
+
+    def release(self, offset: int) -> None:
+        with self.lock:
+            n = self.used.pop(offset)
+            r = sorted(self.free_ranges + [(offset, n)])
+            merged = []
+            for off, length in r:
+                if merged and merged[-1][0] + merged[-1][1] == off:
+                    merged[-1] = (merged[-1][0], merged[-1][1] + length)
+                else:
+                    merged.append((off, length))
+            self.free_ranges = merged
+
+    def in_use(self) -> int:
+        with self.lock:
+            return sum(self.used.values())
+
+    def view(self, offset: int, nbytes: int):
+        """The device bytes [offset, offset + nbytes) as a uint8 tensor."""
+        return self.buf[offset:offset + nbytes]
 
 
 def percentile(values, q: float) -> float | None:
@@ -117,6 +185,7 @@ class Server:
                 t = self.clock()
                 _, info = system.step()
                 out.step_ms.append((self.clock() - t) * 1e3)
+                out.step_start_s.append(t - self._t0)
                 out.energy.append(info["energy"])
                 out.dipole.append(list(info["dipole"]))
                 out.scf_iters.append(info["scf_iters"])
@@ -142,7 +211,7 @@ class Server:
         used = [0]
         active = [0]
         threads = []
-        t0 = self.clock()
+        t0 = self._t0 = self.clock()
 
         def finish(req, o):
             self._work(req, o)
@@ -231,7 +300,7 @@ class BatchedServer:
         groups = {}                                  # group -> worker thread
         reserved = {}                                # group -> bytes held for its batch
         threads = []
-        t0 = self.clock()
+        t0 = self._t0 = self.clock()
 
         def release(o):
             # with cv held
@@ -300,6 +369,7 @@ class BatchedServer:
                 keep, done = [], []
                 for x, info in zip(running, infos):
                     x[1].step_ms.append(dt_ms)
+                    x[1].step_start_s.append(t - t0)
                     x[1].energy.append(info["energy"])
                     x[1].dipole.append(list(info["dipole"]))
                     x[1].scf_iters.append(info["scf_iters"])
@@ -391,13 +461,15 @@ def summarize(outcomes, wall_s: float, dt_au: float, pairs_of) -> dict:
         "fs_per_day": fs / wall_s * 86400.0 if wall_s > 0 else None,
         "pair_solves_per_s": pairs / wall_s if wall_s > 0 else None,
         # one line per request: arrival, admission and finish (s after the start), its
-        # slowest step (index, ms) and SCF iterations (median, max)
+        # slowest step (index, ms, start s) and SCF iterations (median, max)
         "per_request": [
             {"rid": o.rid, "workload": o.workload, "steps": len(o.step_ms), "arrival_s": round(o.arrival_s, 3),
              "admitted_s": None if o.admitted_s is None else round(o.admitted_s, 3),
              "finished_s": None if o.finished_s is None else round(o.finished_s, 3),
              "slowest_step": (None if not o.step_ms else
-                              [int(max(range(len(o.step_ms)), key=o.step_ms.__getitem__)), round(max(o.step_ms), 1)]),
+                              [int(max(range(len(o.step_ms)), key=o.step_ms.__getitem__)), round(max(o.step_ms), 1),
+                               round(o.step_start_s[max(range(len(o.step_ms)), key=o.step_ms.__getitem__)], 3)
+                               if len(o.step_start_s) == len(o.step_ms) else None]),
              "p50_step_ms": None if not o.step_ms else round(percentile(o.step_ms, 0.5), 1),
              "scf_iters": None if not o.scf_iters else [percentile(o.scf_iters, 0.5), max(o.scf_iters)]}
             for o in sorted(outcomes, key=lambda o: o.rid)],
@@ -468,22 +540,53 @@ def batch_reserve(key, precision: str = "mixed") -> int:
     return batch_shape(workload, precision)["tiles_per_launch"] * _pair_tile_bytes(workload, precision) + (64 << 20)
 
 
-def cuda_batch_factory():
-    """make_batch(systems) for BatchedServer: a pt_batch over the systems with the tuned, capped shape."""
+def _arena_block(arena, nbytes):
+    """(offset, uint8 view) of a block of the arena, or (None, None) without an arena or room."""
+    off = arena.alloc(nbytes) if arena is not None else None
+    return (None, None) if off is None else (off, arena.view(off, nbytes))
+
+
+def _release_on_close(obj, arena, off, stream):
+    """After obj.close(): wait for the work on its stream, then return its block to the arena."""
+    close = obj.close
+
+    def close_and_release():
+        try:
+            close()
+        finally:
+            stream.synchronize()
+            arena.release(off)
+
+    obj.close = close_and_release
+
+
+def cuda_batch_factory(arena: DeviceArena | None = None):
+    """make_batch(systems) for BatchedServer: a pt_batch over the systems with the tuned, capped
+    shape, its workspace carved from `arena` when one is given and has room."""
     from .system import Batch
 
     def make_batch(systems):
         shape = batch_shape(systems[0].workload, systems[0].precision)
-        return Batch(systems, pair_tile=shape["pair_tile"], tiles_per_launch=shape["tiles_per_launch"],
-                     priority=stream_priority(systems[0].workload))
+        kw = dict(pair_tile=shape["pair_tile"], tiles_per_launch=shape["tiles_per_launch"])
+        off, ws = _arena_block(arena, Batch.workspace_size(systems, **kw))
+        try:
+            b = Batch(systems, priority=stream_priority(systems[0].workload), workspace=ws, **kw)
+        except Exception:
+            if off is not None:
+                arena.release(off)
+            raise
+        if off is not None:
+            _release_on_close(b, arena, off, b.stream)
+        return b
 
     return make_batch
 
 
-def cuda_backend(device: str = "cuda:0", max_active: int = 8):
+def cuda_backend(device: str = "cuda:0", max_active: int = 8, arena: DeviceArena | None = None):
     """(footprint, open_system) for the CUDA library: one torch stream per slot and priority
-    (stream_priority of the request's workload), the workspace allocated on that stream,
-    start orbitals from the seeded generator."""
+    (stream_priority of the request's workload), the workspace carved from `arena` (or, with
+    no arena or no room in it, allocated on that stream), start orbitals from the seeded
+    generator."""
     import torch
     import synthetic as syn
     from . import _native as nat
@@ -506,8 +609,17 @@ def cuda_backend(device: str = "cuda:0", max_active: int = 8):
         g2 = syn.basis_g2(nat.pt_basis_indices(p), w["n"], w["cell"])
         c0 = syn.initial_coefficients(g2, w["n_orb"], seed=req.seed)
         stream = streams[stream_priority(req.workload)][slot]
-        with torch.cuda.stream(stream):
-            system = System(w, c0, device=str(dev), stream=stream)
+        off, ws = _arena_block(arena, nat.pt_workspace_size(p))
+        try:
+            with torch.cuda.stream(stream):
+                system = System(w, c0, device=str(dev), stream=stream, workspace=ws)
+        except Exception:
+            if off is not None:
+                stream.synchronize()
+                arena.release(off)
+            raise
+        if off is not None:
+            _release_on_close(system, arena, off, stream)
         system.workload, system.precision = req.workload, req.precision
         return system
 
@@ -525,6 +637,8 @@ def main(argv=None) -> None:
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=0.0, help="0: 90%% of the device's free memory")
+    ap.add_argument("--no-arena", dest="arena", action="store_false",
+                    help="allocate each workspace through PyTorch's caching allocator instead of one arena")
     ap.add_argument("--batched", action="store_true",
                     help="12 Si8 + 12 Si64 trajectories, all at t = 0, 20 steps, kicks from seed 1")
     ap.add_argument("--check-alone", action="store_true",
@@ -547,11 +661,13 @@ def main(argv=None) -> None:
         reqs = [Request(d["rid"], d["workload"], d["steps"], d["arrival_s"], seed=d["seed"], precision=args.precision)
                 for d in stream]
     budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else int(0.9 * torch.cuda.mem_get_info()[0])
-    footprint, open_system = cuda_backend(max_active=args.max_active)
+    # the whole budget as one arena: every workspace is carved from it, none allocated while serving
+    arena = DeviceArena(budget, device="cuda:0") if args.arena else None
+    footprint, open_system = cuda_backend(max_active=args.max_active, arena=arena)
     if args.per_request:
         srv = Server(footprint, open_system, budget, args.max_active, keep_orbitals=args.check_alone)
     else:
-        srv = BatchedServer(footprint, open_system, cuda_batch_factory(), budget, args.max_active,
+        srv = BatchedServer(footprint, open_system, cuda_batch_factory(arena), budget, args.max_active,
                             keep_orbitals=args.check_alone, group_of=batch_group,
                             group_reserve=lambda key: batch_reserve(key, args.precision))
     outs = srv.run(reqs)
@@ -561,6 +677,7 @@ def main(argv=None) -> None:
                 "precision": args.precision, "max_active": args.max_active, "budget_bytes": budget,
                 "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes,
                 "scheduling": "per-request" if args.per_request else "continuous batching",
+                "workspaces": "device arena" if arena is not None else "caching allocator",
                 **({} if args.per_request else {"peak_batch": srv.peak_batch, "ticks": srv.ticks,
                                                 "batch_shape": {w: batch_shape(w, args.precision)
                                                                 for w in sorted({r.workload for r in reqs})},

@@ -11,10 +11,12 @@ class System:
 
     params: workload dictionary (see synthetic.si_workload); psi0: (n_orb, npw)
     complex128 start coefficients. The workspace is a torch uint8 tensor on
-    ``device``; all work is enqueued on torch's current stream of that device.
+    ``device`` (allocated here, or passed in as ``workspace``: at least
+    pt_workspace_size bytes, 256-byte aligned, owned by the caller); all work is
+    enqueued on ``stream``, else torch's current stream of that device.
     """
 
-    def __init__(self, params: dict, psi0: np.ndarray, device: str = "cuda:0", stream=None):
+    def __init__(self, params: dict, psi0: np.ndarray, device: str = "cuda:0", stream=None, workspace=None):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -22,7 +24,11 @@ class System:
         self.npw = nat.pt_basis_size(self.params)
         self.n_orb = self.params.n_orb
         self.ws_bytes = nat.pt_workspace_size(self.params)
-        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        if workspace is None:
+            workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        elif workspace.numel() < self.ws_bytes or workspace.dtype != torch.uint8:
+            raise ValueError("workspace: a uint8 device tensor of at least pt_workspace_size bytes is required")
+        self.workspace = workspace
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.handle = nat.pt_init_system(self.params, psi0, self.workspace.data_ptr(), self.ws_bytes,
                                          self.stream.cuda_stream)
@@ -104,17 +110,26 @@ class Batch:
     keeps its own stream. The batch workspace and the stream of the merged pair kernels
     come from PyTorch. pair_tile / tiles_per_launch: the tile edge and launch-group size
     (0: automatic; the autotuner's table gives tuned values). priority: CUDA priority of
-    the batch's stream (0 normal, negative higher).
+    the batch's stream (0 normal, negative higher). workspace: optional caller-owned uint8
+    device tensor of at least the batch workspace size (else one is allocated).
     """
 
-    def __init__(self, systems, pair_tile: int = 0, tiles_per_launch: int = 0, priority: int = 0):
+    @staticmethod
+    def workspace_size(systems, pair_tile: int = 0, tiles_per_launch: int = 0) -> int:
+        return max(256, nat.pt_batch_workspace_size([s.handle for s in systems], pair_tile, tiles_per_launch))
+
+    def __init__(self, systems, pair_tile: int = 0, tiles_per_launch: int = 0, priority: int = 0, workspace=None):
         import torch
         self.torch = torch
         self.systems = list(systems)
         dev = self.systems[0].device
         handles = [s.handle for s in self.systems]
         self.ws_bytes = nat.pt_batch_workspace_size(handles, pair_tile, tiles_per_launch)
-        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        if workspace is None:
+            workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        elif workspace.numel() < max(self.ws_bytes, 256) or workspace.dtype != torch.uint8:
+            raise ValueError("workspace: a uint8 device tensor of at least the batch workspace size is required")
+        self.workspace = workspace
         self.stream = torch.cuda.Stream(dev, priority=priority)
         self.handle = nat.pt_batch_create(handles, pair_tile, tiles_per_launch, self.workspace.data_ptr(),
                                           self.ws_bytes, self.stream.cuda_stream)

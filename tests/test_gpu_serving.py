@@ -66,3 +66,27 @@ def test_continuous_batching_equals_alone(pkg):
         assert len(o.energy) == r.steps
         assert np.array_equal(a.orbitals, o.orbitals)
         assert a.energy == o.energy and a.dipole == o.dipole
+
+
+def test_continuous_batching_from_an_arena_equals_alone(pkg):
+    """The same continuous-batching case with every system and batch workspace carved from
+    one device arena (as the command line serves): results bitwise equal to the request run
+    alone, and every block back in the arena at the end."""
+    from paper_1905_01348_gb300.serve import (BatchedServer, DeviceArena, Request, Server, cuda_backend,
+                                              cuda_batch_factory)
+    kicks = syn.batched_kicks(3, seed=1)
+    reqs = [Request(k, "si8", 2 + k, 0.03 * k, seed=k, kick=tuple(kicks[k])) for k in range(3)]
+    footprint, _ = cuda_backend(max_active=3)
+    budget = 3 * max(footprint(r) for r in reqs) + (1 << 30)
+    arena = DeviceArena(budget, device="cuda:0")
+    footprint, open_system = cuda_backend(max_active=3, arena=arena)
+    srv = BatchedServer(footprint, open_system, cuda_batch_factory(arena), budget, max_active=3, keep_orbitals=True)
+    mix = srv.run(reqs)
+    assert srv.peak_batch >= 2
+    assert arena.in_use() == 0 and arena.free_ranges == [(0, arena.size)]
+    for r, o in zip(reqs, mix):
+        assert o.error is None, o.error
+        (a,) = Server(footprint, open_system, budget, 1, keep_orbitals=True).run([dataclasses.replace(r, arrival_s=0.0)])
+        assert a.error is None, a.error
+        assert np.array_equal(a.orbitals, o.orbitals)
+        assert a.energy == o.energy and a.dipole == o.dipole

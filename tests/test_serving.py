@@ -184,14 +184,33 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
         def __init__(self, device=None, priority=0):
             self.cuda_stream = 0
             self.priority = priority
+            self.synced = 0
+
+        def synchronize(self):
+            self.synced += 1
+
+    class FakeWorkspace:
+        def __init__(self, offset, nbytes):
+            self.offset, self.nbytes = offset, nbytes
+
+    arenas = []
+
+    class HostArena(serve.DeviceArena):
+        """The arena's bookkeeping with host stand-ins for its device views."""
+        def __init__(self, nbytes, device=None, large=1 << 30):
+            super().__init__(nbytes, None, large)
+            arenas.append(self)
+
+        def view(self, offset, nbytes):
+            return FakeWorkspace(offset, nbytes)
 
     made = []
 
     class FakeSystem:
-        def __init__(self, params, psi0, device="cuda:0", stream=None):
+        def __init__(self, params, psi0, device="cuda:0", stream=None, workspace=None):
             assert isinstance(stream, FakeStream) and device == "cuda:0"
             assert psi0.shape[0] == params["n_orb"]
-            self.params, self.psi0, self.k, self.stream = params, psi0, 0, stream
+            self.params, self.psi0, self.k, self.stream, self.workspace = params, psi0, 0, stream, workspace
             made.append(self)
 
         def step(self):
@@ -207,9 +226,14 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     batches = []
 
     class FakeBatch:
-        def __init__(self, systems, pair_tile=0, tiles_per_launch=0, priority=0):
-            self.systems, self.priority = systems, priority
+        def __init__(self, systems, pair_tile=0, tiles_per_launch=0, priority=0, workspace=None):
+            self.systems, self.priority, self.workspace = systems, priority, workspace
+            self.stream = FakeStream()
             batches.append(self)
+
+        @staticmethod
+        def workspace_size(systems, pair_tile=0, tiles_per_launch=0):
+            return 4096 * len(systems)
 
         def step(self):
             return 0, [x.step()[1] for x in self.systems]
@@ -222,6 +246,7 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
     monkeypatch.setattr(system_mod, "System", FakeSystem)
     monkeypatch.setattr(system_mod, "Batch", FakeBatch)
+    monkeypatch.setattr(serve, "DeviceArena", HostArena)
 
     serve.main(["--batched", "--budget-gb", "1000", "--max-active", "4", "--check-alone"])
     res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -236,6 +261,13 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     # the small workloads (batched) run on high-priority streams, their batches too
     assert all(s.stream.priority == -1 for s in firsts)
     assert batches and all(bt.priority == -1 for bt in batches)
+    # every workspace came from the run's arena, and all of it was returned (each after its
+    # stream was synchronised)
+    assert res["workspaces"] == "device arena"
+    assert all(isinstance(s.workspace, FakeWorkspace) for s in firsts)
+    assert all(isinstance(bt.workspace, FakeWorkspace) for bt in batches)
+    assert arenas[0].in_use() == 0 and arenas[0].free_ranges == [(0, arenas[0].size)]
+    assert all(s.stream.synced >= 1 for s in firsts) and all(bt.stream.synced >= 1 for bt in batches)
 
     assert res["scheduling"] == "continuous batching" and res["peak_batch"] >= 2
 
@@ -247,6 +279,7 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     serve.main(["--requests", "3", "--rate", "50", "--steps-max", "6", "--budget-gb", "1000", "--per-request"])
     res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert res["scheduling"] == "per-request" and res["completed"] == 3
+    assert all(len(r["slowest_step"]) == 3 for r in res["per_request"])
 
 
 class SeqBatch:
@@ -337,3 +370,44 @@ def test_batch_policy_of_the_cuda_backend():
     shape = serve.batch_shape("si216", "mixed")
     assert shape["tiles_per_launch"] * 16 * 96 ** 3 * 8 <= serve.BATCH_X_BYTES
     assert serve.batch_reserve("si8") > 0 and serve.batch_reserve(("si216", 2)) <= serve.BATCH_X_BYTES + (64 << 20)
+
+
+def test_device_arena_placement_and_coalescing():
+    """The serving arena's bookkeeping: 256-byte alignment, large blocks from the top and
+    small ones from the bottom, no overlap, None when nothing fits, and released ranges
+    coalescing back into one."""
+    import random
+    from paper_1905_01348_gb300.serve import DeviceArena
+    a = DeviceArena(10_000 + 100, large=2000)
+    assert a.size == 9984                   # rounded down to 256-byte units
+    small = a.alloc(1)                      # rounds up to 256, bottom
+    big = a.alloc(3000)                     # 3072, top
+    assert small == 0 and big == a.size - 3072 and big % 256 == 0
+    assert a.alloc(a.size) is None          # no room for the whole arena any more
+    small2 = a.alloc(300)                   # 512, next to the first small block
+    assert small2 == 256
+    a.release(small)
+    assert a.alloc(256) == 0                # the hole is reused first
+    for off in (0, small2, big):
+        a.release(off)
+    assert a.in_use() == 0 and a.free_ranges == [(0, a.size)]
+    # random alloc / release: blocks never overlap and everything returns
+    rng = random.Random(0)
+    b = DeviceArena(1 << 20, large=1 << 16)
+    live = {}
+    for _ in range(2000):
+        if live and rng.random() < 0.45:
+            off = rng.choice(sorted(live))
+            b.release(off)
+            del live[off]
+        else:
+            n = rng.choice([100, 5000, 70_000, 200_000])
+            off = b.alloc(n)
+            if off is not None:
+                assert off % 256 == 0 and off + n <= b.size
+                for o, m in live.items():
+                    assert off + n <= o or o + m <= off
+                live[off] = n
+    for off in list(live):
+        b.release(off)
+    assert b.free_ranges == [(0, b.size)]
