@@ -50,6 +50,7 @@ pt_status pt_init_system(const pt_params* p, const double* psi0_host, void* d_wo
   const size_t need = carve(nullptr, p, 0);
   if (workspace_bytes < need) { g_last_error = "workspace too small"; return PT_ERR_OOM; }
   pt_system* sys = new pt_system();
+  sys->pinned = pinned_block_get();   // nullptr (plain copies) if page-locked memory is refused
   sys->p = *p;
   if (p->n_atoms > 0) sys->atoms.assign(p->atom_frac, p->atom_frac + 3 * p->n_atoms);
   sys->p.atom_frac = nullptr;
@@ -327,6 +328,7 @@ pt_status pt_destroy(pt_system* sys) {
   if (sys == nullptr) return PT_OK;
   if (sys->ev0) cudaEventDestroy(sys->ev0);
   if (sys->ev1) cudaEventDestroy(sys->ev1);
+  pinned_block_put(sys->pinned);
   std::free(sys->plan_sym.launch_first);
   std::free(sys->plan_sym.launch_count);
   std::free(sys->plan_x.launch_first);

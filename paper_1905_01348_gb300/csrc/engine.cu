@@ -7,6 +7,8 @@
 //   * the start-state relaxation and the RK4 comparison step.
 // All device work is enqueued on the system's stream; host synchronisation
 // happens only where a scalar decides control flow (SCF exit, pivots).
+#include <mutex>
+
 #include "engine.h"
 #include "fft.cuh"
 
@@ -289,11 +291,45 @@ static pt_status gemm32(pt_system* sys, int opA, int opB, int M, int N, int K, d
   return PT_OK;
 }
 
+// Small readbacks land in page-locked memory. With a pageable destination the driver
+// stages the copy through a buffer it shares across the process, and a copy queued behind
+// one stream's long backlog then holds up the readbacks of every other thread's systems.
+namespace {
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+}  // namespace
+
+void* pinned_block_get() {
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  if (g_pinned_free.empty()) {
+    constexpr int kChunk = 64;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, kChunk * kPinnedBytes, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+    for (int k = 0; k < kChunk; ++k) g_pinned_free.push_back(static_cast<unsigned char*>(p) + k * kPinnedBytes);
+  }
+  void* b = g_pinned_free.back();
+  g_pinned_free.pop_back();
+  return b;
+}
+
+void pinned_block_put(void* block) {
+  if (block == nullptr) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.push_back(block);
+}
+
+pt_status read_small(pt_system* sys, void* dst, const void* d_src, size_t bytes) {
+  void* via = (sys->pinned != nullptr && bytes <= kPinnedBytes) ? sys->pinned : dst;
+  PT_CK(cudaMemcpyAsync(via, d_src, bytes, cudaMemcpyDeviceToHost, sys->s));
+  PT_CK(cudaStreamSynchronize(sys->s));
+  if (via != dst) std::memcpy(dst, via, bytes);
+  return PT_OK;
+}
+
 // PT_ERR_TIMEOUT once a tensor-core product has given up a wait (the flag stays set).
 pt_status tc_status(pt_system* sys) {
   int h = 0;
-  PT_CK(cudaMemcpyAsync(&h, sys->status + 4, sizeof(int), cudaMemcpyDeviceToHost, sys->s));
-  PT_CK(cudaStreamSynchronize(sys->s));
+  PT_TRY(read_small(sys, &h, sys->status + 4, sizeof(int)));
   if (h != 0) { sys->err = "tensor-core product: a bounded wait expired"; return PT_ERR_TIMEOUT; }
   return PT_OK;
 }
@@ -357,11 +393,7 @@ pt_status projection(pt_system* sys, const double2* A, double2* HB, bool fp64) {
   return PT_OK;
 }
 
-pt_status read_status(pt_system* sys, int* h) {
-  PT_CK(cudaMemcpyAsync(h, sys->status, sizeof(int), cudaMemcpyDeviceToHost, sys->s));
-  PT_CK(cudaStreamSynchronize(sys->s));
-  return PT_OK;
-}
+pt_status read_status(pt_system* sys, int* h) { return read_small(sys, h, sys->status, sizeof(int)); }
 
 // dst = src L^{-H}, L L^H = src^H src  (Sec. 3.4)
 pt_status orthonormalize(pt_system* sys, const double2* src, double2* dst) {
@@ -444,8 +476,7 @@ pt_status observables(pt_system* sys) {
   PT_CK(pt::energy_sums(sys->rho, sys->vion, sys->vh, sys->p.use_hartree ? 1 : 0, sys->g, sys->p.cell, sys->psi,
                         sys->kin, sys->npw, sys->ne, sys->Mneg, sys->part, sys->red + 8, sys->s));
   double h[8];
-  PT_CK(cudaMemcpyAsync(h, sys->red + 8, sizeof(h), cudaMemcpyDeviceToHost, sys->s));
-  PT_CK(cudaStreamSynchronize(sys->s));
+  PT_TRY(read_small(sys, h, sys->red + 8, sizeof(h)));
   if (sys->mixed) PT_TRY(tc_status(sys));
   const double dV = sys->dV;
   double e = 2.0 * h[6] + dV * h[0];
@@ -638,8 +669,7 @@ pt_status cn_check(pt_system* sys, StepCtx* c) {
     return PT_OK;
   }
   double h = 0.0;
-  PT_CK(cudaMemcpyAsync(&h, sys->red + 1, sizeof(double), cudaMemcpyDeviceToHost, sys->s));
-  PT_CK(cudaStreamSynchronize(sys->s));
+  PT_TRY(read_small(sys, &h, sys->red + 1, sizeof(double)));
   c->drho = h * sys->dV / (2.0 * sys->ne);
   if (c->drho < sys->p.scf_tol) { c->converged = true; c->done = true; return PT_OK; }
   if (c->refine && c->drho < sys->p.scf_fp64_below) c->hi = true;
@@ -668,7 +698,7 @@ pt_status cn_outer(pt_system* sys, StepCtx* c, bool* again) {
 }
 
 pt_status cn_orthonormalize(pt_system* sys, StepCtx* c) {
-  PT_CK(cudaMemcpyAsync(c->hres, sys->red, sizeof(c->hres), cudaMemcpyDeviceToHost, sys->s));
+  PT_TRY(read_small(sys, c->hres, sys->red, sizeof(c->hres)));
   // orthonormalise; the real-space orbitals of Psi_{n+1} for its exchange and density
   PT_TRY(orthonormalize(sys, sys->psi_f, sys->psi));
   PT_TRY(real_orbitals(sys, sys->psi));

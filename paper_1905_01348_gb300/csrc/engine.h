@@ -46,6 +46,9 @@ struct Carver {
 constexpr double kSlater = 0.75;   // times (3/pi)^{1/3}
 
 struct pt_system {
+  // page-locked host block for the small readbacks of a step (read_small); nullptr on the
+  // static path, which allocates nothing and reads back through plain copies
+  void* pinned = nullptr;
   pt_params p{};
   std::vector<double> atoms;
   std::string err;
@@ -174,6 +177,14 @@ pt_status exchange_finish(pt_system* sys, double2* out, int accumulate);
 pt_status exchange_x(pt_system* sys, const double2* X, int ncols, double2* out);
 pt_status tc_status(pt_system* sys);
 pt_status read_status(pt_system* sys, int* h);
+// bytes (at most kPinnedBytes) from the device into dst after the system's stream has
+// reached this point, through the system's page-locked block
+constexpr size_t kPinnedBytes = 256;
+pt_status read_small(pt_system* sys, void* dst, const void* d_src, size_t bytes);
+// page-locked blocks of kPinnedBytes from a process-wide pool (allocated in chunks and
+// kept until exit: freeing page-locked memory can synchronise the device)
+void* pinned_block_get();
+void pinned_block_put(void* block);
 pt_status projection(pt_system* sys, const double2* A, double2* HB, bool fp64 = false);
 pt_status orthonormalize(pt_system* sys, const double2* src, double2* dst);
 pt_status ace_from_w(pt_system* sys, const double2* psi_src = nullptr);
