@@ -274,10 +274,6 @@ pt_status pt_batch_create(pt_system* const* systems, int nsys, int pair_tile, in
   b->plan.d_tiles = d_tiles;
   b->plan.n_tiles = (int)m.tiles.size();
   b->plan.g2_reach = sys[0]->plan_sym.g2_reach;   // the systems share cell and cutoff
-  b->plan.g1_reach = sys[0]->plan_sym.g1_reach;
-  b->plan.ball_r2 = sys[0]->plan_sym.ball_r2;
-  b->plan.ball_dg1 = sys[0]->plan_sym.ball_dg1;
-  b->plan.ball_dg2 = sys[0]->plan_sym.ball_dg2;
   b->ev_sys.assign(sys.size(), nullptr);
   for (size_t i = 0; e == cudaSuccess && i < sys.size(); ++i) e = cudaEventCreateWithFlags(&b->ev_sys[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_batch, cudaEventDisableTiming);

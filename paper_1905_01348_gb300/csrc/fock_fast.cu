@@ -25,6 +25,8 @@ template <int L> struct Cfg { static constexpr int NT13 = 256; };
 template <int L> constexpr int WS = L + 1;   // work-buffer row stride (complex values)
 
 template <int L> constexpr size_t smem13() { return sizeof(float2) * (size_t)(L + NPAIR * RR * WS<L>); }
+// F3 also stages the 2 TT orbital rows of a full tile (RR L values each) behind the work buffer
+template <int L> constexpr size_t smem3() { return smem13<L>() + sizeof(float2) * (size_t)(2 * TT * RR * L); }
 
 // Row layout of the F1 / F3 work buffer: row l (pair p, grid row r) at stride
 // L + 1, and inside each aligned group of 16 elements the 4 x 4 block is
@@ -41,6 +43,10 @@ template <int L> struct RowsT {
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -136,77 +142,62 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 4) k_fast_f1(const PairTile* __r
 // Register-line transforms of 96-point lines (L = 96 = 12 x 8, n = n1 + 12 n2,
 // k = k2 + 8 k1): two threads share a line, thread half h holding n1 in [6h, 6h + 6)
 // (48 values); the partner is the lane XM apart. Used by F2 at 96^3.
-//
-// Frequency rotation. Half h multiplies its inputs by (-1)^(h n2) before its 8-point
-// DFTs over n2, which shifts their outputs by 4h: slot s holds k2 = (s + 4h) mod 8. Then
-// for k2 = 4h + b the value a half keeps is slot b and the one it sends is slot 4 + b for
-// both halves (no per-half selects). Its 12-point input is [own n1, partner's n1], i.e.
-// rotated by 6h, so the 12-point DFT returns (-1)^(h k1) Z[k1]; the inverse consumes that
-// form directly and returns the rotated order the exchange back wants, and the final
-// inverse 8-point DFTs return (-1)^(h n2) x[n1 + 12 n2]. The signs are undone where the
-// line leaves the registers for good.
 namespace l96 {
 constexpr int L = 96, W = L + 1;
 
-// half h's tables (48 entries each): forward twf[8a + s] = W96^((6h + a) ((s + 4h) mod 8)),
-// inverse twi[12b + j] = conj W96^(((j + 6h) mod 12) (4h + b)); every exponent is below 96
-__device__ __forceinline__ float2 twf_entry(const float2* tw, int t) {
-  const int hh = t / 48, a = (t % 48) / 8, sl = t % 8;
-  return tw[(6 * hh + a) * ((sl + 4 * hh) & 7)];
-}
-__device__ __forceinline__ float2 twi_entry(const float2* tw, int t) {
-  const int hh = t / 48, b = (t % 48) / 12, j = t % 12;
-  float2 w = tw[((j + 6 * hh) % 12) * (4 * hh + b)];
-  w.y = -w.y;
-  return w;
-}
+// Twiddle indices n1 k2 stay below 96 (n1 < 12, k2 < 8), so they need no reduction.
 
-// (-1)^(h n2) on the odd n2 (sg = -1 for h = 1)
-__device__ __forceinline__ void modulate(float2 (&v)[6][8], float sg) {
-#pragma unroll
-  for (int a = 0; a < 6; ++a)
-#pragma unroll
-    for (int n2 = 1; n2 < 8; n2 += 2) v[a][n2] = make_float2(sg * v[a][n2].x, sg * v[a][n2].y);
-}
-
-// 8-point DFTs over n2 of the owned n1 = 6h + a, then the twiddle of each slot
-__device__ __forceinline__ void stage_a_fwd(float2 (&v)[6][8], const float2* twf) {
+// 8-point DFTs over n2 of the owned n1 = 6h + a, then the twiddle W96^(n1 k2) (forward)
+__device__ __forceinline__ void stage_a_fwd(float2 (&v)[6][8], int h, const float2* tw) {
+  const int h6 = 6 * h;
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     dft<8, false>(v[a]);
 #pragma unroll
-    for (int sl = 0; sl < 8; ++sl) v[a][sl] = cmul(v[a][sl], twf[8 * a + sl]);
+    for (int k2 = 1; k2 < 8; ++k2) v[a][k2] = cmul(v[a][k2], tw[a * k2 + h6 * k2]);
   }
 }
 
-// inverse 8-point DFTs over the slots: v[a][n2] = (-1)^(h n2) x[6h + a + 12 n2]
+// inverse 8-point DFTs over k2: v[a][n2] = x[6h + a + 12 n2]
 __device__ __forceinline__ void stage_a_inv(float2 (&v)[6][8]) {
 #pragma unroll
   for (int a = 0; a < 6; ++a) dft<8, true>(v[a]);
 }
 
-// k2 = 4h + b: z = [own n1 (slot b), partner's n1 (its slot 4 + b)]
-template <int XM>
-__device__ __forceinline__ void exch_fwd(const float2 (&v)[6][8], int b, float2 (&z)[12]) {
+// forward exchange for k2 = 4h + b: z[n1], n1 = 0..11, from the owned v[.][b or 4 + b] and the partner's
+template <int XM = 1>
+__device__ __forceinline__ void exch_fwd(const float2 (&v)[6][8], int h, int b, float2 (&z)[12]) {
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    z[a] = v[a][b];
-    z[6 + a].x = __shfl_xor_sync(0xffffffffu, v[a][4 + b].x, XM);
-    z[6 + a].y = __shfl_xor_sync(0xffffffffu, v[a][4 + b].y, XM);
+    const float2 mine = h ? v[a][4 + b] : v[a][b];   // my k2 = 4h + b
+    const float2 send = h ? v[a][b] : v[a][4 + b];   // the partner's k2 = 4(1 - h) + b
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, XM);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, XM);
+    z[a] = h ? got : mine;        // n1 = a (owned by half 0)
+    z[6 + a] = h ? mine : got;    // n1 = 6 + a (owned by half 1)
   }
 }
 
-// inverse twiddles of the rotated z (k2 = 4h + b), then own n1 into slot b and the
-// partner's k2 into slot 4 + b
-template <int XM>
-__device__ __forceinline__ void exch_inv(float2 (&z)[12], int b, const float2* twi, float2 (&v)[6][8]) {
+// inverse twiddle of Z[n1][k2], k2 = 4h + b, then the exchange back into v[a][b], v[a][4 + b]
+template <int XM = 1>
+__device__ __forceinline__ void exch_inv(float2 (&z)[12], int h, int b, const float2* tw, float2 (&v)[6][8]) {
+  const int h4 = 4 * h;
 #pragma unroll
-  for (int j = 0; j < 12; ++j) z[j] = cmul(z[j], twi[12 * b + j]);
+  for (int n1 = 1; n1 < 12; ++n1) {
+    float2 w = tw[n1 * b + n1 * h4];
+    w.y = -w.y;
+    z[n1] = cmul(z[n1], w);
+  }
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    v[a][b] = z[a];
-    v[a][4 + b].x = __shfl_xor_sync(0xffffffffu, z[6 + a].x, XM);
-    v[a][4 + b].y = __shfl_xor_sync(0xffffffffu, z[6 + a].y, XM);
+    const float2 mine = h ? z[6 + a] : z[a];          // my n1 = 6h + a
+    const float2 send = h ? z[a] : z[6 + a];          // the partner's n1
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, XM);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, XM);  // my n1, the partner's k2 = 4(1 - h) + b
+    v[a][b] = h ? got : mine;
+    v[a][4 + b] = h ? mine : got;
   }
 }
 }  // namespace l96
@@ -276,46 +267,35 @@ __global__ void __launch_bounds__(Cfg2<L>::NT, Cfg2<L>::MINB) k_fast_f2(float2* 
 // points of n1 in [6h, 6h + 6) (48 values). Forward: 8-point DFTs over n2 in registers
 // (twiddle W96^(n1 k2)), then the two halves exchange by warp shuffles so that half h
 // holds k2 in [4h, 4h + 4) for all twelve n1, and 12-point DFTs over n1 give the outputs
-// k2 + 8 k1 (in the rotated form of namespace l96). The inverse runs the same steps
-// backwards. The slab arrives by cp.async into a shared buffer (rows padded to 97) and
-// leaves from it; between the passes the lines cross shared memory once per pass instead
-// of once per radix stage. Column pass: for each owned k2, forward 12-point DFT, kernel
-// multiply, inverse 12-point DFT, all in registers; only the columns (axis-1 frequency at
-// this axis-2 frequency) inside the pair ball are transformed, the others are set to zero
-// (the pair products have no component there), and warps with no live column skip it.
-// Signs: row i0 leaves the column pass as (-1)^(h0 n2_0) times its values (i0 = 6 h0 + a
-// + 12 n2_0), and the row inverse adds (-1)^(h n2) along i1; both are undone at the store.
-template <int L>
-constexpr size_t smem2r() { return sizeof(float2) * (size_t)(4 * 48 + L * WS<L>); }
+// k2 + 8 k1. The inverse runs the same steps backwards. The slab arrives by cp.async
+// into a shared buffer (rows padded to 97) and leaves from it; between the passes the
+// lines cross shared memory once per pass instead of once per radix stage. Column
+// pass: for each owned k2, forward 12-point DFT, kernel multiply, inverse 12-point DFT,
+// all in registers.
 
 template <int L>
 __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, const PairTile* __restrict__ tiles,
                                                      int tile0, const float* __restrict__ khat_t,
-                                                     const float2* __restrict__ tw_g, int reach, float ball_r2,
-                                                     float dg1, float dg2) {
+                                                     const float2* __restrict__ tw_g, int reach) {
   static_assert(L == l96::L, "register-line F2 is written for 96-point lines");
   using namespace l96;
   constexpr int SLAB = L * L;
   constexpr int XM = 16;                      // the two halves of a line are the lanes 16 apart
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* twf = reinterpret_cast<float2*>(smem_raw);   // [2][48]
-  float2* twi = twf + 96;                               // [2][48]
-  float2* buf = twi + 96;                               // [row][W]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* buf = tw + L;                       // [row][W]
+  const int tid = threadIdx.x, lane = tid & 31;
   // a half-warp holds the same half h of 16 consecutive lines: its shared-memory accesses
   // (one row of 16 lines, or 16 columns of one row) fall on distinct banks
-  const int line = warp * 16 + (lane & 15), h = lane >> 4;
-  const float sg = h ? -1.f : 1.f;
+  const int line = (tid >> 5) * 16 + (lane & 15), h = lane >> 4;
   const int slot = blockIdx.y;
   if (slot % NPAIR >= tiles[tile0 + slot / NPAIR].n_pairs) return;
   const int i2 = (int)blockIdx.x <= reach ? (int)blockIdx.x : (int)blockIdx.x + (L - (int)gridDim.x);
-  twf[tid] = tid < 96 ? twf_entry(tw_g, tid) : twi_entry(tw_g, tid - 96);   // 192 threads, 192 entries
+  for (int t = tid; t < L; t += 192) tw[t] = tw_g[t];
   float2* slab = X + ((long)slot * L + i2) * SLAB;
   for (int e = tid; e < SLAB; e += 192) cp_async8(buf + (e / L) * W + e % L, slab + e);
   cp_async_wait_all();
   __syncthreads();
-  const float2* twf_h = twf + 48 * h;
-  const float2* twi_h = twi + 48 * h;
   float2 v[6][8];
   // ---- forward along axis 1 (rows): v[a][n2] = x[6h + a + 12 n2] of row `line`; outputs
   // k = k2 + 8 k1 back into the row
@@ -324,53 +304,40 @@ __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, con
 #pragma unroll
     for (int a = 0; a < 6; ++a) v[a][n2] = buf[line * W + 6 * h + a + 12 * n2];
   __syncthreads();   // every row is in registers before any is overwritten
-  modulate(v, sg);
-  stage_a_fwd(v, twf_h);
+  stage_a_fwd(v, h, tw);
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     float2 z[12];
-    exch_fwd<XM>(v, b, z);
+    exch_fwd<XM>(v, h, b, z);
     dft12<false>(z);
 #pragma unroll
     for (int k1 = 0; k1 < 12; ++k1) buf[line * W + 4 * h + b + 8 * k1] = z[k1];
   }
   __syncthreads();
-  // ---- axis 0 (columns): forward, kernel multiply, inverse, in registers. Columns with
-  // signed frequency |f1| <= m are live: lines 0..m and m+1..2m take columns 0..m and
-  // L-m..L-1, lines 2m+1.. take the dead columns m+1..L-m-1 and zero them.
+  // ---- axis 0 (columns): column c = line; forward, kernel multiply, inverse, in registers
   {
-    int n_live = L, m = L / 2;
-    if (ball_r2 > 0.f) {
-      const float f2 = (float)(i2 < L / 2 ? i2 : i2 - L) * dg2;
-      m = min(L / 2 - 1, (int)floorf(sqrtf(fmaxf(ball_r2 - f2 * f2, 0.f)) / dg1) + 1);   // one column of margin
-      n_live = 2 * m + 1;
-    }
-    const int c = (n_live >= L || line <= m) ? line : (line < n_live ? line + (L - n_live) : line - n_live + m + 1);
-    if (warp * 16 < n_live) {   // warp-uniform: the shuffles below need the whole warp
-#pragma unroll
-      for (int n2 = 0; n2 < 8; ++n2)
-#pragma unroll
-        for (int a = 0; a < 6; ++a) v[a][n2] = buf[(6 * h + a + 12 * n2) * W + c];
-      modulate(v, sg);
-      stage_a_fwd(v, twf_h);
-      const float* kt = khat_t + (long)i2 * SLAB + c;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        float2 z[12];
-        exch_fwd<XM>(v, b, z);
-        dft12<false>(z);                                   // frequency k0 = 4h + b + 8 k1 along axis 0
-#pragma unroll
-        for (int k1 = 0; k1 < 12; ++k1) z[k1] = cscale(z[k1], __ldg(kt + (4 * h + b + 8 * k1) * L));
-        dft12<true>(z);
-        exch_inv<XM>(z, b, twi_h, v);
-      }
-      stage_a_inv(v);
-    }
-    const bool live = line < n_live;
+    const int c = line;
 #pragma unroll
     for (int n2 = 0; n2 < 8; ++n2)
 #pragma unroll
-      for (int a = 0; a < 6; ++a) buf[(6 * h + a + 12 * n2) * W + c] = live ? v[a][n2] : make_float2(0.f, 0.f);
+      for (int a = 0; a < 6; ++a) v[a][n2] = buf[(6 * h + a + 12 * n2) * W + c];
+    stage_a_fwd(v, h, tw);
+    const float* kt = khat_t + (long)i2 * SLAB + c;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float2 z[12];
+      exch_fwd<XM>(v, h, b, z);
+      dft12<false>(z);                                   // frequency k0 = 4h + b + 8 k1 along axis 0
+#pragma unroll
+      for (int k1 = 0; k1 < 12; ++k1) z[k1] = cscale(z[k1], __ldg(kt + (4 * h + b + 8 * k1) * L));
+      dft12<true>(z);                                    // back to n1, this k2
+      exch_inv<XM>(z, h, b, tw, v);
+    }
+    stage_a_inv(v);
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) buf[(6 * h + a + 12 * n2) * W + c] = v[a][n2];
   }
   __syncthreads();
   // ---- inverse along axis 1 (rows): inputs k2 + 8 k1 of row `line`, outputs back into it
@@ -380,21 +347,14 @@ __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, con
 #pragma unroll
     for (int k1 = 0; k1 < 12; ++k1) z[k1] = buf[line * W + 4 * h + b + 8 * k1];
     dft12<true>(z);
-    exch_inv<XM>(z, b, twi_h, v);
+    exch_inv<XM>(z, h, b, tw, v);
   }
   stage_a_inv(v);
   __syncthreads();   // every row is in registers before any is overwritten
-  {
-    // undo (-1)^(h0 n2_0) of the row (i0 = line) and (-1)^(h n2) along it
-    const float s_row = ((line % 12) >= 6 && ((line / 12) & 1)) ? -1.f : 1.f;
-    const float s_odd = s_row * sg;
 #pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) {
-      const float sn = (n2 & 1) ? s_odd : s_row;
+  for (int n2 = 0; n2 < 8; ++n2)
 #pragma unroll
-      for (int a = 0; a < 6; ++a) buf[line * W + 6 * h + a + 12 * n2] = make_float2(sn * v[a][n2].x, sn * v[a][n2].y);
-    }
-  }
+    for (int a = 0; a < 6; ++a) buf[line * W + 6 * h + a + 12 * n2] = v[a][n2];
   __syncthreads();
   for (int e = tid; e < SLAB; e += 192) slab[e] = buf[(e / L) * W + e % L];
 }
@@ -436,20 +396,29 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const PairTile* __r
       else cp_async8(dst, xp + (long)i2 * L * L);
     }
   }
+  // a full tile's eight orbital rows (RR L contiguous values each) arrive with the pair
+  // intermediate, so the accumulation below reads them from shared memory
+  float2* orb_s = work + NPAIR * RR * WS<L>;
+  const bool full = full_tile(tl);
+  if (full)
+    for (int t = tid; t < 2 * TT * (ROW / 2); t += NT) {
+      const int o = t / (ROW / 2), e2 = 2 * (t % (ROW / 2));
+      cp_async16(orb_s + o * ROW + e2, orb_ptr(tl, o) + roff + e2);
+    }
   cp_async_wait_all();
   __syncthreads();
   ct_inverse_lay<float2, L, NPAIR * RR, NT, A>(work, np * RR, tw, tid);
-  if (full_tile(tl)) {
+  if (full) {
     // off-diagonal 4 x 4 tile: output a (< 4) takes psi_{4+b} conj(v_ab) over b, output
-    // 4 + b takes psi_a v_ab over a, in the order of the contribution lists; all orbital
-    // and W loads of an element are issued together
+    // 4 + b takes psi_a v_ab over a, in the order of the contribution lists; the W loads
+    // of an element are issued together
     for (int e = tid; e < ROW; e += NT) {
       const int row = e / L, col = e % L;
       float2 v[2 * TT], w[2 * TT];
       float2* dst[2 * TT];
 #pragma unroll
       for (int o = 0; o < 2 * TT; ++o) {
-        v[o] = __ldg(orb_ptr(tl, o) + roff + e);
+        v[o] = orb_s[o * ROW + e];
         dst[o] = tl.is_out[o] ? acc_ptr(tl, o) + roff + e : nullptr;
         if (tl.is_out[o]) w[o] = *dst[o];
       }
@@ -496,12 +465,12 @@ static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* 
   if (const unsigned long long bit = device_bit_todo(attr_done)) {
     cudaError_t e = cudaFuncSetAttribute(k_fast_f1<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_fast_f3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
+    e = cudaFuncSetAttribute(k_fast_f3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3<L>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f2<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
     if (e != cudaSuccess) return e;
     if constexpr (L == 96) {
-      e = cudaFuncSetAttribute(k_fast_f2r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r<L>());
+      e = cudaFuncSetAttribute(k_fast_f2r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
       if (e != cudaSuccess) return e;
     }
     attr_done.fetch_or(bit, std::memory_order_release);
@@ -509,18 +478,14 @@ static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* 
   float2* X = (float2*)scratch;
   const int reach = 2 * plan.g2_reach + 1 < L ? plan.g2_reach : L;
   const int n_live = reach >= L ? L : 2 * reach + 1;
-  // column skipping in F2 needs alias-free products along axes 1 and 2
-  const float ball_r2 = (reach < L && 2 * plan.g1_reach + 1 < L) ? plan.ball_r2 : 0.f;
   for (int l = 0; l < plan.n_launch; ++l) {
     const int t0 = plan.launch_first[l], nt = plan.launch_count[l];
     dim3 g13((unsigned)(L * (L / RR)), (unsigned)nt);
     k_fast_f1<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     dim3 g2((unsigned)n_live, (unsigned)(nt * NPAIR));
-    if constexpr (L == 96)
-      k_fast_f2r<L><<<g2, 192, smem2r<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach, ball_r2, plan.ball_dg1,
-                                                 plan.ball_dg2);
+    if constexpr (L == 96) k_fast_f2r<L><<<g2, 192, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
     else k_fast_f2<L><<<g2, Cfg2<L>::NT, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
-    k_fast_f3<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
+    k_fast_f3<L><<<g13, Cfg<L>::NT13, smem3<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     launched(3);
   }
   return cudaGetLastError();

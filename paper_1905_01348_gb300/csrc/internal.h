@@ -120,12 +120,6 @@ struct FockPlan {
   // exactly beyond it on an alias-free grid, so the fast path skips those
   // axis-2 slabs. A value >= n2 / 2 disables the skip.
   int g2_reach;
-  // The same along axis 1, and the ball |G| <= 2 max |G| of the basis that holds every
-  // pair product's frequencies: ball_r2 = (2 max |G|)^2, ball_dg1 / ball_dg2 = 2 pi / cell
-  // along axes 1 and 2. On an alias-free grid the 96^3 F2 skips the axis-0 transforms of
-  // the (axis-1, axis-2) frequency columns outside the ball; ball_r2 = 0 disables it.
-  int g1_reach;
-  float ball_r2, ball_dg1, ball_dg2;
 };
 
 // The pair kernels of `plan` (tiles bound to their orbitals and accumulators).

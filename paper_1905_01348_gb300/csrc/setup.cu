@@ -77,26 +77,14 @@ static long fock_points(const pt_params* p) {
   return (long)q.n[0] * q.n[1] * q.n[2];
 }
 
-// The reach of pair products (Eq. 3: products of two basis-limited orbitals): twice the
-// largest |g1| and |g2| index of the basis along axes 1 and 2, and the ball of twice the
-// largest |G| (|G_a - G_b| <= |G_a| + |G_b|).
+// The reach of pair products along axis 2 (Eq. 3: products of two basis-limited
+// orbitals): twice the largest |g2| index of the basis.
 void set_pair_reach(pt::FockPlan* plan, const pt_params* p) {
   std::vector<int> idx;
-  std::vector<double> g2;
-  basis_list(p, &idx, &g2);
-  int m1 = 0, m2 = 0;
-  double gmax2 = 0.0;
-  for (size_t k = 0; k < idx.size(); ++k) {
-    const int v = idx[k];
-    m2 = std::max(m2, std::abs(freq(v % p->n[2], p->n[2])));
-    m1 = std::max(m1, std::abs(freq((v / p->n[2]) % p->n[1], p->n[1])));
-    gmax2 = std::max(gmax2, g2[k]);
-  }
-  plan->g2_reach = 2 * m2;
-  plan->g1_reach = 2 * m1;
-  plan->ball_r2 = (float)(4.0 * gmax2);
-  plan->ball_dg1 = (float)(2.0 * M_PI / p->cell[1]);
-  plan->ball_dg2 = (float)(2.0 * M_PI / p->cell[2]);
+  basis_list(p, &idx, nullptr);
+  int m = 0;
+  for (int v : idx) m = std::max(m, std::abs(freq(v % p->n[2], p->n[2])));
+  plan->g2_reach = 2 * m;
 }
 
 // Screened kernel K(G) = 4 pi (1 - exp(-G^2 / (4 w^2))) / G^2, K(0) = pi / w^2 (its limit),
