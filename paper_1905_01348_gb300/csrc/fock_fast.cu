@@ -25,8 +25,6 @@ template <int L> struct Cfg { static constexpr int NT13 = 256; };
 template <int L> constexpr int WS = L + 1;   // work-buffer row stride (complex values)
 
 template <int L> constexpr size_t smem13() { return sizeof(float2) * (size_t)(L + NPAIR * RR * WS<L>); }
-// F3 also stages the 2 TT orbital rows of a full tile (RR L values each) behind the work buffer
-template <int L> constexpr size_t smem3() { return smem13<L>() + sizeof(float2) * (size_t)(2 * TT * RR * L); }
 
 // Row layout of the F1 / F3 work buffer: row l (pair p, grid row r) at stride
 // L + 1, and inside each aligned group of 16 elements the 4 x 4 block is
@@ -43,10 +41,6 @@ template <int L> struct RowsT {
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -396,29 +390,20 @@ __global__ void __launch_bounds__(Cfg<L>::NT13, 3) k_fast_f3(const PairTile* __r
       else cp_async8(dst, xp + (long)i2 * L * L);
     }
   }
-  // a full tile's eight orbital rows (RR L contiguous values each) arrive with the pair
-  // intermediate, so the accumulation below reads them from shared memory
-  float2* orb_s = work + NPAIR * RR * WS<L>;
-  const bool full = full_tile(tl);
-  if (full)
-    for (int t = tid; t < 2 * TT * (ROW / 2); t += NT) {
-      const int o = t / (ROW / 2), e2 = 2 * (t % (ROW / 2));
-      cp_async16(orb_s + o * ROW + e2, orb_ptr(tl, o) + roff + e2);
-    }
   cp_async_wait_all();
   __syncthreads();
   ct_inverse_lay<float2, L, NPAIR * RR, NT, A>(work, np * RR, tw, tid);
-  if (full) {
+  if (full_tile(tl)) {
     // off-diagonal 4 x 4 tile: output a (< 4) takes psi_{4+b} conj(v_ab) over b, output
-    // 4 + b takes psi_a v_ab over a, in the order of the contribution lists; the W loads
-    // of an element are issued together
+    // 4 + b takes psi_a v_ab over a, in the order of the contribution lists; all orbital
+    // and W loads of an element are issued together
     for (int e = tid; e < ROW; e += NT) {
       const int row = e / L, col = e % L;
       float2 v[2 * TT], w[2 * TT];
       float2* dst[2 * TT];
 #pragma unroll
       for (int o = 0; o < 2 * TT; ++o) {
-        v[o] = orb_s[o * ROW + e];
+        v[o] = __ldg(orb_ptr(tl, o) + roff + e);
         dst[o] = tl.is_out[o] ? acc_ptr(tl, o) + roff + e : nullptr;
         if (tl.is_out[o]) w[o] = *dst[o];
       }
@@ -465,7 +450,7 @@ static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* 
   if (const unsigned long long bit = device_bit_todo(attr_done)) {
     cudaError_t e = cudaFuncSetAttribute(k_fast_f1<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_fast_f3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3<L>());
+    e = cudaFuncSetAttribute(k_fast_f3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem13<L>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fast_f2<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<L>());
     if (e != cudaSuccess) return e;
@@ -485,7 +470,7 @@ static cudaError_t launch_fast(const FockPlan& plan, const float* khat_t, void* 
     dim3 g2((unsigned)n_live, (unsigned)(nt * NPAIR));
     if constexpr (L == 96) k_fast_f2r<L><<<g2, 192, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
     else k_fast_f2<L><<<g2, Cfg2<L>::NT, smem2<L>(), s>>>(X, plan.d_tiles, t0, khat_t, tw, reach);
-    k_fast_f3<L><<<g13, Cfg<L>::NT13, smem3<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
+    k_fast_f3<L><<<g13, Cfg<L>::NT13, smem13<L>(), s>>>(plan.d_tiles, t0, X, tw, reach);
     launched(3);
   }
   return cudaGetLastError();

@@ -547,15 +547,22 @@ def _arena_block(arena, nbytes):
 
 
 def _release_on_close(obj, arena, off, stream):
-    """After obj.close(): wait for the work on its stream, then return its block to the arena."""
+    """After obj.close(): wait for the work on its stream, then return its block to the arena,
+    once. (close() runs again from __del__ when the object is collected, by then perhaps
+    after the arena has handed the same offset to another workspace.)"""
     close = obj.close
+    lock = threading.Lock()
+    released = [False]
 
     def close_and_release():
         try:
             close()
         finally:
-            stream.synchronize()
-            arena.release(off)
+            with lock:
+                if not released[0]:
+                    released[0] = True
+                    stream.synchronize()
+                    arena.release(off)
 
     obj.close = close_and_release
 

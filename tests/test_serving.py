@@ -411,3 +411,37 @@ def test_device_arena_placement_and_coalescing():
     for off in list(live):
         b.release(off)
     assert b.free_ranges == [(0, b.size)]
+
+
+def test_arena_block_is_released_once():
+    """A workspace wrapper closed twice (explicitly, then again from __del__ after the arena
+    has given the same offset to the next workspace) returns its block only once."""
+    from paper_1905_01348_gb300 import serve
+
+    class Stream:
+        def __init__(self):
+            self.synced = 0
+
+        def synchronize(self):
+            self.synced += 1
+
+    class Obj:
+        def __init__(self):
+            self.closed = 0
+
+        def close(self):
+            self.closed += 1
+
+    arena = serve.DeviceArena(1 << 20, large=1 << 30)
+    a, sa = Obj(), Stream()
+    off_a = arena.alloc(4096)
+    serve._release_on_close(a, arena, off_a, sa)
+    a.close()
+    off_b = arena.alloc(4096)              # the freed range is handed out again
+    assert off_b == off_a
+    a.close()                              # the late second close must not free b's block
+    assert arena.in_use() == 4096 and sa.synced == 1 and a.closed == 2
+    b = Obj()
+    serve._release_on_close(b, arena, off_b, Stream())
+    b.close()
+    assert arena.in_use() == 0
