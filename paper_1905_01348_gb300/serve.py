@@ -37,6 +37,11 @@ batches come from the autotuner's table (tuning.json), the launch-group size cap
 so that a batch's pair intermediate stays within 4 GiB, which the admission budget
 reserves while the group runs. `--per-request` runs every request on its own thread and stream
 instead, with no shared launches.
+
+The small workloads (those that are batched) run on high-priority streams, so their
+kernels are dispatched ahead of a large request's queued step. Every workspace is carved
+from one device arena allocated at start-up (`--no-arena`: one PyTorch allocation per
+workspace instead), so nothing is allocated or freed on the device while requests run.
 """
 from __future__ import annotations
 
