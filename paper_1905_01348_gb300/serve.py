@@ -39,9 +39,11 @@ reserves while the group runs. `--per-request` runs every request on its own thr
 instead, with no shared launches.
 
 The small workloads (those that are batched) run on high-priority streams, so their
-kernels are dispatched ahead of a large request's queued step. Every workspace is carved
-from one device arena allocated at start-up (`--no-arena`: one PyTorch allocation per
-workspace instead), so nothing is allocated or freed on the device while requests run.
+kernels are dispatched ahead of a large request's queued step, and the process asks for
+32 hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS), so that streams do not share one.
+Every workspace is carved from one device arena allocated at start-up (`--no-arena`: one
+PyTorch allocation per workspace instead), so nothing is allocated or freed on the device
+while requests run.
 """
 from __future__ import annotations
 
@@ -50,10 +52,23 @@ import collections
 import dataclasses
 import json
 import math
+import os
 import threading
 import time
 
 FS_AU = 41.341374575751   # atomic units of time per femtosecond
+
+# Hardware work queues per process. CUDA multiplexes streams onto this many queues (8
+# unless the environment says otherwise); two streams on one queue run in submission
+# order, so a small request's kernels would wait behind a large request's queued step.
+# The server uses up to 2 x max_active slot streams plus one per running batch.
+HW_QUEUES = 32
+
+
+def use_all_hw_queues() -> None:
+    """Ask for HW_QUEUES hardware queues; effective only before CUDA is initialised in this
+    process (a value already in the environment is kept)."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", str(HW_QUEUES))
 
 
 @dataclasses.dataclass
@@ -639,6 +654,7 @@ def cuda_backend(device: str = "cuda:0", max_active: int = 8, arena: DeviceArena
 
 
 def main(argv=None) -> None:
+    use_all_hw_queues()
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--requests", type=int, default=12)
     ap.add_argument("--rate", type=float, default=4.0, help="mean arrivals per second (Poisson)")

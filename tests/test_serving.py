@@ -247,6 +247,7 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     monkeypatch.setattr(system_mod, "System", FakeSystem)
     monkeypatch.setattr(system_mod, "Batch", FakeBatch)
     monkeypatch.setattr(serve, "DeviceArena", HostArena)
+    monkeypatch.delenv("CUDA_DEVICE_MAX_CONNECTIONS", raising=False)   # main() sets it; restored afterwards
 
     serve.main(["--batched", "--budget-gb", "1000", "--max-active", "4", "--check-alone"])
     res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -445,3 +446,18 @@ def test_arena_block_is_released_once():
     serve._release_on_close(b, arena, off_b, Stream())
     b.close()
     assert arena.in_use() == 0
+
+
+def test_command_line_asks_for_all_hardware_queues(monkeypatch):
+    """The server's streams must not share hardware queues: main() sets
+    CUDA_DEVICE_MAX_CONNECTIONS before anything initialises CUDA, keeping a value the
+    environment already gives."""
+    from paper_1905_01348_gb300 import serve
+    monkeypatch.delenv("CUDA_DEVICE_MAX_CONNECTIONS", raising=False)
+    serve.use_all_hw_queues()
+    import os
+    assert os.environ["CUDA_DEVICE_MAX_CONNECTIONS"] == str(serve.HW_QUEUES) == "32"
+    assert 2 * 8 + 8 <= serve.HW_QUEUES          # slot streams of both priorities + batches
+    monkeypatch.setenv("CUDA_DEVICE_MAX_CONNECTIONS", "4")
+    serve.use_all_hw_queues()
+    assert os.environ["CUDA_DEVICE_MAX_CONNECTIONS"] == "4"
