@@ -22,8 +22,10 @@
  *   device workspace of at least pt_workspace_size() bytes (256-byte aligned)
  *   and a cudaStream_t (as void*, NULL = default stream); the library never
  *   allocates device memory and enqueues all device work on that stream.
- *   Host pointers are borrowed for the duration of the call. The workspace
- *   must stay valid until pt_destroy.
+ *   Each system takes one 256-byte page-locked host block from a process-wide
+ *   pool (allocated in chunks of 64, kept until exit) for its step readbacks;
+ *   pt_exchange_static takes none. Host pointers are borrowed for the duration
+ *   of the call. The workspace must stay valid until pt_destroy.
  * Errors: every call returns pt_status. On failure nothing is aborted;
  *   pt_last_error() gives a message. A failed step leaves the orbitals at the
  *   last consistent state. Calls that return host data synchronise the stream.

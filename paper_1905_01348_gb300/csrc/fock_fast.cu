@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(192, 2) k_fast_f2r(float2* __restrict__ X, con
   using namespace l96;
   constexpr int SLAB = L * L;
   constexpr int XM = 16;                      // the two halves of a line are the lanes 16 apart
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* buf = tw + L;                       // [row][W]
   const int tid = threadIdx.x, lane = tid & 31;
