@@ -115,7 +115,7 @@ class DeviceArena:
 
     ALIGN = 256
 
-    def __init__(self, nbytes: int, device=None, large: int = 1 << 30):
+    def __init__(self, nbytes: int, device=None, large: int = 8 << 30):
         self.size = int(nbytes) // self.ALIGN * self.ALIGN
         self.large = int(large)
         self.free_ranges = [(0, self.size)] if self.size > 0 else []   # sorted by offset
@@ -587,6 +587,15 @@ def _release_on_close(obj, arena, off, stream):
     obj.close = close_and_release
 
 
+def arena_bytes(budget: int, small_blocks, free_bytes: int) -> int:
+    """Size of the serving arena: the admission budget plus room for two of the largest blocks
+    placed from the bottom, so that holes left between small blocks (a Si64 workspace of 3.2
+    GB freed between batch workspaces of 4 GB) cannot stop a placement that the byte budget
+    admitted; at most 97% of the free device memory."""
+    slack = 2 * max(small_blocks, default=0)
+    return min(int(budget) + slack, int(0.97 * free_bytes))
+
+
 def cuda_batch_factory(arena: DeviceArena | None = None):
     """make_batch(systems) for BatchedServer: a pt_batch over the systems with the tuned, capped
     shape, its workspace carved from `arena` when one is given and has room."""
@@ -689,8 +698,11 @@ def main(argv=None) -> None:
         reqs = [Request(d["rid"], d["workload"], d["steps"], d["arrival_s"], seed=d["seed"], precision=args.precision)
                 for d in stream]
     budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else int(0.9 * torch.cuda.mem_get_info()[0])
-    # the whole budget as one arena: every workspace is carved from it, none allocated while serving
-    arena = DeviceArena(budget, device="cuda:0") if args.arena else None
+    # the budget (plus placement slack) as one arena: every workspace is carved from it, none is
+    # allocated while serving; the largest blocks placed from the bottom are the batch workspaces
+    small = [batch_reserve(w, args.precision) for w in sorted({r.workload for r in reqs})]
+    arena = (DeviceArena(arena_bytes(budget, small, torch.cuda.mem_get_info()[0]), device="cuda:0")
+             if args.arena else None)
     footprint, open_system = cuda_backend(max_active=args.max_active, arena=arena)
     if args.per_request:
         srv = Server(footprint, open_system, budget, args.max_active, keep_orbitals=args.check_alone)

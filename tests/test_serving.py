@@ -248,6 +248,7 @@ def test_cuda_backend_glue_and_cli_on_host(monkeypatch, capsys):
     monkeypatch.setattr(system_mod, "Batch", FakeBatch)
     monkeypatch.setattr(serve, "DeviceArena", HostArena)
     monkeypatch.delenv("CUDA_DEVICE_MAX_CONNECTIONS", raising=False)   # main() sets it; restored afterwards
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (2000 << 30, 2000 << 30))
 
     serve.main(["--batched", "--budget-gb", "1000", "--max-active", "4", "--check-alone"])
     res = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -461,3 +462,32 @@ def test_command_line_asks_for_all_hardware_queues(monkeypatch):
     monkeypatch.setenv("CUDA_DEVICE_MAX_CONNECTIONS", "4")
     serve.use_all_hw_queues()
     assert os.environ["CUDA_DEVICE_MAX_CONNECTIONS"] == "4"
+
+
+def test_arena_slack_keeps_admitted_blocks_placeable():
+    """Near full use, holes between small blocks can stop a placement the byte budget admits
+    (a 3.2 GB workspace freed between 4 GB batch blocks leaves a hole no batch fits); the
+    arena's slack of two of the largest small blocks removes that, within the free memory."""
+    from paper_1905_01348_gb300 import serve
+    G = 1 << 30
+    small, sys64 = 4 * G, 3276 << 20              # 256-byte multiples
+    budget = 2 * (small + sys64) + sys64          # filled exactly below
+
+    def fill(arena):
+        # [Si64][batch][Si64][batch][Si64] up to the budget, then every Si64 block leaves:
+        # 8 GB in use, three separate 3.2 GB holes
+        s64 = [arena.alloc(sys64)]
+        for _ in range(2):
+            arena.alloc(small)
+            s64.append(arena.alloc(sys64))
+        for o in s64:
+            arena.release(o)
+        return 2 * small
+
+    tight = serve.DeviceArena(budget, large=8 * G)
+    used = fill(tight)
+    assert used + small <= budget and tight.alloc(small) is None       # admitted, not placeable
+    roomy = serve.DeviceArena(serve.arena_bytes(budget, [small, sys64], free_bytes=100 * G), large=8 * G)
+    fill(roomy)
+    assert roomy.alloc(small) is not None
+    assert serve.arena_bytes(budget, [small], free_bytes=21 * G) == int(0.97 * 21 * G)   # capped by free memory
