@@ -62,36 +62,10 @@ def main(argv=None) -> None:
     p = make_params(base)
     g2 = syn.basis_g2(nat.pt_basis_indices(p), base["n"], base["cell"])
     C0 = syn.initial_coefficients(g2, base["n_orb"], seed=args.seed)
-    runs = {}
-    if args.ace_vs_exact:
-        cases = [("exact", "fp64", args.tight_tol, "exact", 0), ("ace", "fp64", args.tight_tol, "ace", 0),
-                 ("ace_outer1", "fp64", args.tight_tol, "ace", 1), ("ace_outer2", "fp64", args.tight_tol, "ace", 2),
-                 ("mixed_ace", "mixed", base["scf_tol"], "ace", 0)]
-        for name, prec, tol, mode, outer in cases:
-            s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200, fock_mode=mode, ace_outer=outer), C0)
-            e0, d0 = s.observables()
-            rec = {"energy": [e0], "dipole": [np.asarray(d0)], "scf": [], "ms": []}
-            for _ in range(args.steps):
-                t0 = time.perf_counter()
-                st, info = s.step()
-                rec["ms"].append((time.perf_counter() - t0) * 1e3)
-                rec["energy"].append(info["energy"])
-                rec["dipole"].append(np.asarray(info["dipole"]))
-                rec["scf"].append(info["scf_iters"])
-            rec["psi"] = s.orbitals()
-            s.close()
-            runs[name] = rec
-    else:
-        cases = [("fp64", "fp64", base["scf_tol"], None), ("mixed", "mixed", base["scf_tol"], None),
-             ("fp64_tight", "fp64", args.tight_tol, None)]
-    if args.mixed_tight_tol > 0:
-        cases.append(("mixed_tight", "mixed", args.mixed_tight_tol, None))
-    refine = base["scf_fp64_below"] if args.refine_below is None else args.refine_below
-    if args.fock_grid:
-        cases.append(("mixed_fock", "mixed", base["scf_tol"], (args.fock_grid,) * 3))
-    for name, prec, tol, fock in ([] if args.ace_vs_exact else cases):
-        s = System(dict(base, precision=prec, scf_tol=tol, scf_max=200, fock_grid=fock,
-                        scf_fp64_below=refine if name == "mixed_tight" else base["scf_fp64_below"]), C0)
+    def run(**overrides):
+        """One trajectory of args.steps PT-CN steps from C0 with the workload's parameters
+        changed by `overrides`: energies, dipoles, SCF iterations, step times, final orbitals."""
+        s = System(dict(base, scf_max=200, **overrides), C0)
         e0, d0 = s.observables()
         rec = {"energy": [e0], "dipole": [np.asarray(d0)], "scf": [], "ms": []}
         for _ in range(args.steps):
@@ -103,7 +77,24 @@ def main(argv=None) -> None:
             rec["scf"].append(info["scf_iters"])
         rec["psi"] = s.orbitals()
         s.close()
-        runs[name] = rec
+        return rec
+
+    refine = base["scf_fp64_below"] if args.refine_below is None else args.refine_below
+    if args.ace_vs_exact:
+        tight = dict(precision="fp64", scf_tol=args.tight_tol)
+        cases = {"exact": dict(tight, fock_mode="exact", ace_outer=0), "ace": dict(tight, fock_mode="ace", ace_outer=0),
+                 "ace_outer1": dict(tight, fock_mode="ace", ace_outer=1),
+                 "ace_outer2": dict(tight, fock_mode="ace", ace_outer=2),
+                 "mixed_ace": dict(precision="mixed", scf_tol=base["scf_tol"], fock_mode="ace", ace_outer=0)}
+    else:
+        cases = {"fp64": dict(precision="fp64", scf_tol=base["scf_tol"]),
+                 "mixed": dict(precision="mixed", scf_tol=base["scf_tol"]),
+                 "fp64_tight": dict(precision="fp64", scf_tol=args.tight_tol)}
+        if args.mixed_tight_tol > 0:
+            cases["mixed_tight"] = dict(precision="mixed", scf_tol=args.mixed_tight_tol, scf_fp64_below=refine)
+        if args.fock_grid:
+            cases["mixed_fock"] = dict(precision="mixed", scf_tol=base["scf_tol"], fock_grid=(args.fock_grid,) * 3)
+    runs = {name: run(**kw) for name, kw in cases.items()}
 
     def compare(a, b):
         de = [abs(x - y) / n_atoms for x, y in zip(a["energy"], b["energy"])]
