@@ -111,6 +111,9 @@ typedef struct pt_params {
    * exchange every iteration by one, at the cost of one exchange per rebuild. 0: ACE once
    * per step. */
   int ace_outer;
+  /* Seed of the start coefficients pt_init_system generates when psi0_host is NULL
+   * (pt_seeded_coefficients). */
+  uint64_t seed;
 } pt_params;
 
 typedef struct pt_system pt_system;
@@ -132,11 +135,23 @@ pt_status pt_basis_size(const pt_params* p, int* npw);
  * out_host must hold npw entries. */
 pt_status pt_basis_indices(const pt_params* p, int64_t* out_host);
 
+/* Seeded start coefficients (host only, no device): out_host receives n_orb x npw
+ * complex128 values (band-major, interleaved re/im), not orthonormal. Coefficient m
+ * of band b is (g1 + i g2) exp(-|G_m|^2 / 4) with (g1, g2) standard normals by the
+ * Box-Muller transform of the uniforms u1 = U(2j), u2 = U(2j + 1), j = b npw + m:
+ * g1 = sqrt(-2 ln u1) cos(2 pi u2), g2 = sqrt(-2 ln u1) sin(2 pi u2). U(k) =
+ * ((x_k >> 11) + 0.5) 2^-53, x_k the (k + 1)-th output of SplitMix64 (Steele, Lea and
+ * Flood, 2014) started from the state p->seed: state += 0x9E3779B97F4A7C15; z = state;
+ * z = (z ^ (z >> 30)) 0xBF58476D1CE4E5B9; z = (z ^ (z >> 27)) 0x94D049BB133111EB;
+ * x = z ^ (z >> 31). A stand-in for the paper's ground state (Sec. 4), as any start. */
+pt_status pt_seeded_coefficients(const pt_params* p, double* out_host);
+
 /* Device workspace bytes pt_init_system needs for these parameters. */
 pt_status pt_workspace_size(const pt_params* p, size_t* bytes);
 
 /* Create a system (Eq. 5 state). psi0_host: n_orb x npw complex128 initial
- * coefficients (need not be orthonormal). They are orthonormalised by
+ * coefficients (need not be orthonormal), or NULL for pt_seeded_coefficients of
+ * p->seed. They are orthonormalised by
  * Cholesky (Sec. 3.4), relaxed by relax_iters preconditioned steepest-descent
  * steps on the local Hamiltonian of a Kerker-mixed density (a stand-in for
  * the ground state the paper starts from), and the exchange data of the

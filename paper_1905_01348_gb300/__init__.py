@@ -9,7 +9,7 @@ from ._native import (PT_FOCK_ACE, PT_FOCK_EXACT, PT_FOCK_NONE, PT_FP64, PT_MIXE
                       pt_orbitals_device, pt_propagate, pt_set_orbitals, pt_workspace_size, pt_set_timing,
                       pt_get_timing, pt_launch_count, pt_exchange_static, pt_get_state, pt_set_state, pt_rk4_step,
                       pt_complex_product, pt_batch_workspace_size, pt_batch_create, pt_batch_exchange,
-                      pt_batch_step, pt_batch_set_timing, pt_batch_get_timing, pt_batch_destroy)
+                      pt_batch_step, pt_batch_set_timing, pt_batch_get_timing, pt_batch_destroy, pt_seeded_coefficients)
 from .system import Batch, System
 
 __all__ = ["PT_FOCK_ACE", "PT_FOCK_EXACT", "PT_FOCK_NONE", "PT_FP64", "PT_MIXED", "PtError", "PtParams", "PtStepInfo",
@@ -18,4 +18,4 @@ __all__ = ["PT_FOCK_ACE", "PT_FOCK_EXACT", "PT_FOCK_NONE", "PT_FP64", "PT_MIXED"
            "pt_observables", "pt_orbitals_device", "pt_propagate", "pt_set_orbitals", "pt_workspace_size",
            "pt_set_timing", "pt_get_timing", "pt_launch_count", "pt_exchange_static", "pt_complex_product", "pt_get_state",
            "pt_set_state", "pt_rk4_step", "Batch", "pt_batch_workspace_size", "pt_batch_create", "pt_batch_exchange",
-           "pt_batch_step", "pt_batch_set_timing", "pt_batch_get_timing", "pt_batch_destroy"]
+           "pt_batch_step", "pt_batch_set_timing", "pt_batch_get_timing", "pt_batch_destroy", "pt_seeded_coefficients"]

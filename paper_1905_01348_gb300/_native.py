@@ -57,6 +57,7 @@ class PtParams(C.Structure):
         ("n_fock", C.c_int * 3),
         ("scf_fp64_below", C.c_double),
         ("ace_outer", C.c_int),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -98,6 +99,7 @@ def load() -> C.CDLL:
     sig = {
         "pt_basis_size": (C.c_int, [P, C.POINTER(C.c_int)]),
         "pt_basis_indices": (C.c_int, [P, C.POINTER(C.c_int64)]),
+        "pt_seeded_coefficients": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pt_workspace_size": (C.c_int, [P, C.POINTER(C.c_size_t)]),
         "pt_init_system": (C.c_int, [P, C.POINTER(C.c_double), vp, C.c_size_t, vp, C.POINTER(vp)]),
         "pt_build_ace": (C.c_int, [vp]),
@@ -187,6 +189,7 @@ def make_params(d: dict) -> PtParams:
         p.laser_dir[k] = float(ld[k])
     p.scf_fp64_below = float(d.get("scf_fp64_below", 0.0))
     p.ace_outer = int(d.get("ace_outer", 0))
+    p.seed = int(d.get("seed", 0))
     nf = d.get("fock_grid") or (0, 0, 0)
     for k in range(3):
         p.n_fock[k] = int(nf[k])
@@ -210,17 +213,29 @@ def pt_basis_indices(params: PtParams) -> np.ndarray:
     return out
 
 
+def pt_seeded_coefficients(params: PtParams) -> np.ndarray:
+    """The start coefficients pt_init_system generates from params.seed, (n_orb, npw) complex128."""
+    out = np.zeros((params.n_orb, pt_basis_size(params)), dtype=np.complex128)
+    _check(load().pt_seeded_coefficients(C.byref(params), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
 def pt_workspace_size(params: PtParams) -> int:
     n = C.c_size_t(0)
     _check(load().pt_workspace_size(C.byref(params), C.byref(n)))
     return n.value
 
 
-def pt_init_system(params: PtParams, psi0: np.ndarray, d_workspace: int, workspace_bytes: int, stream: int = 0):
-    psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+def pt_init_system(params: PtParams, psi0, d_workspace: int, workspace_bytes: int, stream: int = 0):
+    """psi0: (n_orb, npw) complex128 start coefficients, or None for those of params.seed."""
+    if psi0 is None:
+        ptr = C.POINTER(C.c_double)()
+    else:
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+        ptr = psi0.ctypes.data_as(C.POINTER(C.c_double))
     h = C.c_void_p()
-    _check(load().pt_init_system(C.byref(params), psi0.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(d_workspace),
-                                 C.c_size_t(workspace_bytes), C.c_void_p(stream), C.byref(h)))
+    _check(load().pt_init_system(C.byref(params), ptr, C.c_void_p(d_workspace), C.c_size_t(workspace_bytes),
+                                 C.c_void_p(stream), C.byref(h)))
     return h
 
 

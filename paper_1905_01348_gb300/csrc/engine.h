@@ -148,6 +148,8 @@ void basis_list(const pt_params* p, std::vector<int>* idx, std::vector<double>* 
 pt_params fock_params(const pt_params* p);   // the parameters with the Fock grid as the grid
 bool fock_is_own(const pt_params* p);
 void set_pair_reach(pt::FockPlan* plan, const pt_params* p);
+// pt_seeded_coefficients: n_orb x npw complex128 (interleaved) from p->seed
+void seeded_coefficients(const pt_params* p, double* out);
 int choose_tile(const pt_params* p);
 int tiles_per_launch(const pt_params* p, long N, bool mixed);
 int h_batch(const pt_params* p);

@@ -77,6 +77,36 @@ static long fock_points(const pt_params* p) {
   return (long)q.n[0] * q.n[1] * q.n[2];
 }
 
+// k-th output (k = 0, 1, ...) of SplitMix64 started from the state `seed` (Steele, Lea
+// and Flood, 2014): the state advances by the golden-ratio increment, the output is its
+// variant-13 mix. Counter-based: output k depends only on seed and k.
+static inline uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// the top 53 bits as a uniform number in (0, 1), never 0
+static inline double unit_open(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
+
+void seeded_coefficients(const pt_params* p, double* out) {
+  std::vector<int> idx;
+  std::vector<double> g2;
+  basis_list(p, &idx, &g2);
+  const uint64_t npw = idx.size();
+  for (int b = 0; b < p->n_orb; ++b)
+    for (uint64_t m = 0; m < npw; ++m) {
+      const uint64_t j = (uint64_t)b * npw + m;
+      const double u1 = unit_open(splitmix64_at(p->seed, 2 * j));
+      const double u2 = unit_open(splitmix64_at(p->seed, 2 * j + 1));
+      const double r = std::sqrt(-2.0 * std::log(u1)), t = 2.0 * M_PI * u2;
+      const double w = std::exp(-0.25 * g2[m]);
+      out[2 * j] = r * std::cos(t) * w;
+      out[2 * j + 1] = r * std::sin(t) * w;
+    }
+}
+
 // The reach of pair products along axis 2 (Eq. 3: products of two basis-limited
 // orbitals): twice the largest |g2| index of the basis.
 void set_pair_reach(pt::FockPlan* plan, const pt_params* p) {
@@ -375,9 +405,15 @@ pt_status init_body(pt_system* sys, const double* psi0_host) {
     PT_CK(pt::ion_potential(sys->vion, sys->g, p->cell, sys->d_atoms, p->n_atoms, p->well_depth, p->well_sigma, s));
   else
     PT_CK(cudaMemsetAsync(sys->vion, 0, sizeof(double) * sys->N, s));
-  // start orbitals
-  if (psi0_host == nullptr) { sys->err = "psi0_host is NULL"; return PT_ERR_INVALID; }
+  // start orbitals: the caller's, or the seeded ones (kept alive until the copy has landed)
+  std::vector<double> seeded;
+  if (psi0_host == nullptr) {
+    seeded.resize(2 * (size_t)npw * sys->ne);
+    seeded_coefficients(p, seeded.data());
+    psi0_host = seeded.data();
+  }
   PT_CK(cudaMemcpyAsync(sys->tmp, psi0_host, sizeof(double2) * npw * sys->ne, cudaMemcpyHostToDevice, s));
+  if (!seeded.empty()) PT_CK(cudaStreamSynchronize(s));
   PT_TRY(orthonormalize(sys, sys->tmp, sys->psi));
   PT_TRY(relax(sys));
   PT_TRY(state_from_psi(sys));

@@ -10,13 +10,14 @@ class System:
     """Owns one pt_system handle and the device workspace it runs in.
 
     params: workload dictionary (see synthetic.si_workload); psi0: (n_orb, npw)
-    complex128 start coefficients. The workspace is a torch uint8 tensor on
-    ``device`` (allocated here, or passed in as ``workspace``: at least
+    complex128 start coefficients, or None for the library's seeded ones
+    (pt_seeded_coefficients of params["seed"]). The workspace is a torch uint8
+    tensor on ``device`` (allocated here, or passed in as ``workspace``: at least
     pt_workspace_size bytes, 256-byte aligned, owned by the caller); all work is
     enqueued on ``stream``, else torch's current stream of that device.
     """
 
-    def __init__(self, params: dict, psi0: np.ndarray, device: str = "cuda:0", stream=None, workspace=None):
+    def __init__(self, params: dict, psi0, device: str = "cuda:0", stream=None, workspace=None):
         import torch
         self.torch = torch
         self.device = torch.device(device)

@@ -98,6 +98,37 @@ def initial_coefficients(g2_basis: np.ndarray, n_orb: int, seed: int) -> np.ndar
     return (z[..., 0] + 1j * z[..., 1]) * np.exp(-g2 / 4.0)[None, :]
 
 
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, k: np.ndarray) -> np.ndarray:
+    """Outputs k (0, 1, ...) of SplitMix64 (Steele, Lea and Flood, 2014) started from the
+    state `seed`: state_k = seed + (k + 1) * golden (mod 2^64), mixed by the variant-13
+    finaliser (shifts 30, 27, 31; multipliers 0xBF58476D1CE4E5B9, 0x94D049BB133111EB).
+    Counter-based: each output depends only on seed and k."""
+    k = np.asarray(k, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(int(seed) % (1 << 64)) + (k + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_coefficients(g2_basis: np.ndarray, n_orb: int, seed: int) -> np.ndarray:
+    """The start coefficients the library generates when it is given no orbitals
+    (pt_seeded_coefficients), shape (n_orb, n_basis), complex128: coefficient m of band b
+    is (g1 + i g2) exp(-|G_m|^2 / 4), (g1, g2) the Box-Muller normals of the uniforms
+    u1 = U(2j), u2 = U(2j + 1), j = b n_basis + m, U(k) = ((x_k >> 11) + 1/2) 2^-53 from
+    SplitMix64 output x_k. Rows are not orthonormal."""
+    g2 = np.asarray(g2_basis, dtype=np.float64)
+    j = np.arange(int(n_orb) * g2.size, dtype=np.uint64)
+    u = lambda x: ((x >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    u1, u2 = u(splitmix64(seed, 2 * j)), u(splitmix64(seed, 2 * j + np.uint64(1)))
+    r, t = np.sqrt(-2.0 * np.log(u1)), 2.0 * np.pi * u2
+    z = (r * np.cos(t) + 1j * r * np.sin(t)).reshape(int(n_orb), g2.size)
+    return z * np.exp(-g2 / 4.0)[None, :]
+
+
 def batched_kicks(count: int, seed: int = 1) -> np.ndarray:
     """Kick vectors for a batch of trajectories: axis uniform over x/y/z, size U[0.005, 0.02]."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))
