@@ -35,7 +35,7 @@ pt_status pt_seeded_coefficients(const pt_params* p, double* out_host) {
   std::string why;
   pt_status st = check_params(p, &why);
   if (st != PT_OK) { g_last_error = why; return st; }
-  if (out_host == nullptr) { g_last_error = "out is NULL"; return PT_ERR_INVALID; }
+  if (out_host == nullptr) { g_last_error = "pt_seeded_coefficients: out is NULL"; return PT_ERR_INVALID; }
   seeded_coefficients(p, out_host);
   return PT_OK;
 }

@@ -75,3 +75,11 @@ def test_system_without_orbitals_equals_seeded_coefficients(pkg):
     assert np.array_equal(a.orbitals(), b.orbitals())
     a.close()
     b.close()
+
+
+def test_seeded_coefficients_null_output_is_refused(pkg):
+    import ctypes
+    lib = pkg.load()
+    p = pkg.make_params(syn.si_workload("si8"))
+    assert lib.pt_seeded_coefficients(ctypes.byref(p), None) == 1          # PT_ERR_INVALID
+    assert pkg.pt_last_error(None).startswith("pt_seeded_coefficients:")
