@@ -1,8 +1,8 @@
 """PT-CN steps on the Si64 (64^3) and Si216 (96^3) cells against the FP64 oracle.
 
 The workloads' own cells, grids, cutoffs and time step, with few orbitals so the oracle
-finishes in seconds: the cubic pair kernels of these grids (the 96^3 register-line F2 with
-its column skip included), the sphere-pruned transforms of 43,819 planewaves, and the whole
+finishes in seconds: the cubic pair kernels of these grids (the 96^3 register-line F2
+included), the sphere-pruned transforms of 43,819 planewaves, and the whole
 step (ACE once per step, fixed SCF iterations) run through the C ABI. Tolerances as in
 test_gpu_parity.py: 1e-10 relative on the FP64 path; the mixed path within 1e-4 on the
 orbitals and 1e-6 relative on the energy (FP32 rounding through the fixed iterations).
