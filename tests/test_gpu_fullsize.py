@@ -4,8 +4,10 @@ times, on sampled outputs the oracle computes one by one.
 
 Both sides orthonormalise the same seeded coefficients (no relaxation, which
 the oracle could not afford at this size). The GPU applies the exchange to
-all 432 orbitals with the pair pipeline; the oracle computes three sampled
-columns V_X psi_j (every i, summed over chunks of orbitals) with dense FFTs.
+all 432 orbitals with the pair pipeline; the oracle computes six sampled
+columns V_X psi_j (every i, summed over chunks of orbitals) with dense FFTs:
+the first, both sides of a pair-tile edge (orbitals 3 and 4), one from the
+middle and the last two (the last tile).
 Tolerances as in test_gpu_parity: 2e-5 (mixed) and 1e-10 (FP64).
 """
 import os
@@ -20,7 +22,7 @@ from oracle import ptcn as pc
 
 pytestmark = pytest.mark.gpu
 
-SAMPLES = (0, 217, 431)
+SAMPLES = (0, 3, 4, 217, 430, 431)
 
 
 @pytest.fixture(scope="module")
